@@ -1,0 +1,161 @@
+/*
+ * corr.h -- C ABI of the GB300 X-engine (libcorr.so).
+ *
+ * The X-engine of an FX correlator (Sec. 2.3 of the paper "Design and
+ * Implementation of a Scalable Correlator Based on ROACH2+GPU Cluster for
+ * Tianlai 96-Dual-Polarization Antenna Array") performs, for every frequency
+ * channel c, conjugate multiplication and accumulation (CMAC) over all input
+ * pairs:
+ *
+ *     V_c[i][j] = sum_t x_c,i(t) * conj(x_c,j(t)),   i >= j          (Eq. 2)
+ *
+ * over the lower triangle including the autos, N(N+1)/2 products per channel
+ * (Eq. 1), integrated over many blocks (Sec. 2.4: ~4 s integrations), with a
+ * full-Stokes output (abstract, Sec. 1).
+ *
+ * Conventions shared by every call:
+ *   - Inputs: N = n_ant * n_pol, input index i = n_pol * antenna + pol
+ *     (pol 0 = X, pol 1 = Y).
+ *   - Samples: one byte per complex sample, 4-bit two's complement real part
+ *     in the high nibble and imaginary part in the low nibble (Sec. 2.1's
+ *     4-bit + 4-bit requantised F-engine output).  All 256 byte values are
+ *     valid, -8 included.
+ *   - Block layout: uint8 x[n_chan][N][block_len] (channel-major "corner
+ *     turned" order, Sec. 2.1's Transpose module).
+ *   - Visibility layout: int64 vis[n_chan][P][2], P = N(N+1)/2, pair index
+ *     i(i+1)/2 + j for i >= j, element 0 = real, 1 = imaginary.
+ *   - Stokes layout (n_pol == 2): int64 stokes[n_chan][A][4][2],
+ *     A = n_ant(n_ant+1)/2, antenna-pair index p(p+1)/2 + q for p >= q,
+ *     order I, Q, U, V with
+ *         XX = V[2p][2q], YY = V[2p+1][2q+1], XY = V[2p][2q+1], YX = V[2p+1][2q]
+ *         (p == q: XY = conj(V[2p+1][2p]))
+ *         I = XX + YY, Q = XX - YY, U = XY + YX, V = -j (XY - YX)   (no 1/2).
+ *   - All arithmetic is integer and exact: results do not depend on block
+ *     order or launch configuration.
+ *   - Device pointers are CUDA device (or managed) addresses owned by the
+ *     caller; host pointers are ordinary host memory (pinned memory makes the
+ *     copies faster).  `stream` is a cudaStream_t (NULL = legacy default).
+ *   - Every call returns CORR_OK (0) or a negative CORR_E* code; on error
+ *     nothing is enqueued.  corr_strerror() names the code.
+ *   - Thread safety: one context may be used by one host thread at a time,
+ *     with all its device calls on one stream.  Independent contexts are
+ *     independent.
+ */
+#ifndef CORR_H
+#define CORR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CORR_OK 0
+#define CORR_EINVAL (-1)   /* bad argument (size, pointer, alignment, n_pol) */
+#define CORR_ENOMEM (-2)   /* device or host allocation failed */
+#define CORR_ECUDA (-3)    /* a CUDA runtime or driver call failed */
+#define CORR_EARCH (-4)    /* current device is not compute capability 10.3 */
+#define CORR_ETIMEOUT (-5) /* a device-side wait ran out; results are void */
+#define CORR_ESTATE (-6)   /* call not valid in the context's current state */
+
+/* Largest block_len accepted.  Each block is accumulated in fp32 inside the
+ * tensor-core accumulator before it is folded into int64; a block of L samples
+ * bounds every partial sum by 128 * L, which stays an exactly representable
+ * integer (< 2^24) for L <= 131071. */
+#define CORR_MAX_BLOCK_LEN 131071
+/* Largest input count N = n_ant * n_pol accepted. */
+#define CORR_MAX_INPUTS 8192
+
+typedef struct corr_ctx corr_ctx;
+
+/*
+ * Creates a correlator for n_ant antennas with n_pol (1 or 2) polarisations,
+ * n_chan channels and blocks of block_len samples per channel (Sec. 2.3; the
+ * paper's system is n_ant = 96, n_pol = 2, n_chan = 1024 over 125 MHz,
+ * Sec. 2.2).  Allocates the int64 integration buffer on the current device
+ * (n_chan * P * 16 bytes, zeroed) and a few kilobytes of bookkeeping.
+ * On success *out owns them until corr_destroy.
+ * Errors: CORR_EINVAL (non-positive size, n_pol not 1/2, block_len above
+ * CORR_MAX_BLOCK_LEN, N above CORR_MAX_INPUTS, out NULL), CORR_EARCH,
+ * CORR_ENOMEM, CORR_ECUDA.
+ */
+int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out);
+
+/*
+ * Integrates one block: for every channel, every i >= j,
+ *   acc[c][i(i+1)/2 + j] += sum_{t < block_len} x[c][i][t] * conj(x[c][j][t]).
+ * d_block: device pointer to uint8[n_chan][N][block_len], 16-byte aligned.
+ * Stream-ordered and asynchronous; d_block must stay valid and unchanged until
+ * the stream has executed the call.
+ * Errors: CORR_EINVAL (NULL ctx/d_block, misaligned d_block), CORR_ECUDA.
+ */
+int corr_push_block(corr_ctx *ctx, const uint8_t *d_block, void *stream);
+
+/*
+ * Ends the integration: writes the visibilities accumulated since the last
+ * dump to d_vis (int64[n_chan][P][2]) if it is not NULL, the full-Stokes
+ * products to d_stokes (int64[n_chan][A][4][2]) if it is not NULL, and zeroes
+ * the integration buffer.  Stream-ordered and asynchronous.
+ * Errors: CORR_EINVAL (NULL ctx; d_stokes given with n_pol == 1),
+ * CORR_ECUDA.
+ */
+int corr_dump(corr_ctx *ctx, int64_t *d_vis, int64_t *d_stokes, void *stream);
+
+/*
+ * Host-buffer variants.  corr_push_block_host copies h_block
+ * (uint8[n_chan][N][block_len] in host memory) into a context-owned device
+ * staging slot and integrates it on `stream`; it returns once h_block has been
+ * copied, so the caller may reuse it, while the correlation itself may still
+ * be running (the copy of the next block overlaps it).  corr_dump_host dumps
+ * into context-owned device buffers and copies them to h_vis / h_stokes
+ * (either may be NULL), returning when the host buffers are filled.  The
+ * staging and output buffers are allocated on first use and freed by
+ * corr_destroy.
+ * Errors: as the device variants, plus CORR_ENOMEM.
+ */
+int corr_push_block_host(corr_ctx *ctx, const uint8_t *h_block, void *stream);
+int corr_dump_host(corr_ctx *ctx, int64_t *h_vis, int64_t *h_stokes, void *stream);
+
+/*
+ * Sizes: *vis_elems = n_chan * P * 2, *stokes_elems = n_chan * A * 8 (0 when
+ * n_pol == 1), *samples_integrated = samples per channel pushed since the last
+ * dump.  Any output pointer may be NULL.
+ */
+int corr_sizes(const corr_ctx *ctx, size_t *vis_elems, size_t *stokes_elems,
+               long long *samples_integrated);
+
+/*
+ * Waits for `stream`, then reads the context's device status word.  Returns
+ * CORR_OK, CORR_ETIMEOUT if a device-side wait ran out since the last
+ * successful check (the integration is then void and should be dumped and
+ * discarded), or CORR_ECUDA.  Clears the status word.
+ */
+int corr_check(corr_ctx *ctx, void *stream);
+
+/*
+ * Host-only view of the tile schedule for n_in inputs (no device needed).
+ * cover, if not NULL, is uint8[n_in][n_in] and receives +1 for every element
+ * (i, j) that the schedule's MMAs fold into the integration buffer (the lower
+ * triangle, each element exactly once).  *n_units receives the work units per
+ * channel and *issued_cmacs the complex MACs per channel per sample that the
+ * MMAs issue (lower triangle plus the padding they also compute; the useful
+ * count is n_in(n_in+1)/2).  Errors: CORR_EINVAL (n_in out of range).
+ */
+int corr_plan(int n_in, uint8_t *cover, int *n_units, long long *issued_cmacs);
+
+/* Number of kernel launches the context has enqueued (pushes and dumps). */
+long long corr_launch_count(const corr_ctx *ctx);
+
+/* Releases everything the context owns.  The caller must have synchronised
+ * every stream that used it.  NULL is ignored. */
+void corr_destroy(corr_ctx *ctx);
+
+/* Static string naming a CORR_* code. */
+const char *corr_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CORR_H */

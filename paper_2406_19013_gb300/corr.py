@@ -1,0 +1,196 @@
+"""Python binding of libcorr (include/corr.h): argument marshalling only.
+
+Every step of the X-engine runs in the library's CUDA kernels; this module
+passes device pointers (torch tensors' ``data_ptr()``), host pointers (numpy
+arrays) and the current CUDA stream, and turns negative return codes into
+exceptions.  There is no fallback: if the library is missing the import of
+this module's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcorr.so")
+
+CORR_OK = 0
+CORR_EINVAL = -1
+CORR_ENOMEM = -2
+CORR_ECUDA = -3
+CORR_EARCH = -4
+CORR_ETIMEOUT = -5
+CORR_ESTATE = -6
+CORR_MAX_BLOCK_LEN = 131071
+CORR_MAX_INPUTS = 8192
+
+# (name, restype, argtypes) of every function include/corr.h declares
+_vp, _ci, _ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+ABI = [
+    ("corr_create", _ci, [_ci, _ci, _ci, _ci, ctypes.POINTER(_vp)]),
+    ("corr_push_block", _ci, [_vp, _vp, _vp]),
+    ("corr_dump", _ci, [_vp, _vp, _vp, _vp]),
+    ("corr_push_block_host", _ci, [_vp, _vp, _vp]),
+    ("corr_dump_host", _ci, [_vp, _vp, _vp, _vp]),
+    ("corr_sizes", _ci, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                         ctypes.POINTER(_ll)]),
+    ("corr_check", _ci, [_vp, _vp]),
+    ("corr_plan", _ci, [_ci, _vp, ctypes.POINTER(_ci), ctypes.POINTER(_ll)]),
+    ("corr_launch_count", _ll, [_vp]),
+    ("corr_destroy", None, [_vp]),
+    ("corr_strerror", ctypes.c_char_p, [_ci]),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class CorrError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+def load(path: str = LIB_PATH):
+    """Loads libcorr.so (built by ``paper_2406_19013_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: run paper_2406_19013_gb300.build.build()")
+            lib = ctypes.CDLL(path)
+            for name, res, args in ABI:
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return load().corr_strerror(code).decode()
+
+
+def _ck(rc: int, what: str):
+    if rc != CORR_OK:
+        raise CorrError(rc, what)
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def plan(n_in: int, with_cover: bool = False):
+    """(units per channel, issued CMACs per channel-sample, cover or None)."""
+    cover = np.zeros((n_in, n_in), dtype=np.uint8) if with_cover else None
+    nu, iss = _ci(), _ll()
+    _ck(load().corr_plan(n_in, cover.ctypes.data if with_cover else None, ctypes.byref(nu),
+                         ctypes.byref(iss)), "corr_plan")
+    return nu.value, iss.value, cover
+
+
+def n_pairs(n_in: int) -> int:
+    return n_in * (n_in + 1) // 2
+
+
+class Correlator:
+    """One X-engine integration context on the current CUDA device.
+
+    ``push_block`` integrates a uint8[n_chan][n_inputs][block_len] device
+    tensor; ``dump`` returns (vis int64[n_chan][P][2], stokes
+    int64[n_chan][A][4][2] or None) and restarts the integration.
+    """
+
+    def __init__(self, n_ant: int, n_pol: int, n_chan: int, block_len: int):
+        self._lib = load()
+        h = _vp()
+        _ck(self._lib.corr_create(n_ant, n_pol, n_chan, block_len, ctypes.byref(h)), "corr_create")
+        self._h = h
+        self.n_ant, self.n_pol, self.n_chan, self.block_len = n_ant, n_pol, n_chan, block_len
+        self.n_in = n_ant * n_pol
+        self.n_pairs = n_pairs(self.n_in)
+        self.n_apairs = n_pairs(n_ant)
+
+    # ---------------------------------------------------------------- device
+    def push_block(self, block, stream=None):
+        import torch
+        if isinstance(block, torch.Tensor):
+            if not (block.is_cuda and block.dtype == torch.uint8 and block.is_contiguous()):
+                raise ValueError("block must be a contiguous uint8 CUDA tensor")
+            if block.numel() != self.n_chan * self.n_in * self.block_len:
+                raise ValueError("block has the wrong number of samples")
+            ptr = block.data_ptr()
+        else:
+            ptr = int(block)
+        _ck(self._lib.corr_push_block(self._h, ptr, _stream_handle(stream)), "corr_push_block")
+
+    def dump(self, vis=None, stokes=None, want_vis: bool = True, want_stokes: bool | None = None,
+             stream=None):
+        import torch
+        if want_stokes is None:
+            want_stokes = self.n_pol == 2
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if vis is None and want_vis:
+            vis = torch.empty((self.n_chan, self.n_pairs, 2), dtype=torch.int64, device=dev)
+        if stokes is None and want_stokes:
+            stokes = torch.empty((self.n_chan, self.n_apairs, 4, 2), dtype=torch.int64, device=dev)
+        _ck(self._lib.corr_dump(self._h, vis.data_ptr() if vis is not None else None,
+                                stokes.data_ptr() if stokes is not None else None,
+                                _stream_handle(stream)), "corr_dump")
+        return vis, stokes
+
+    # ---------------------------------------------------------------- host
+    def push_block_host(self, block: np.ndarray, stream=None):
+        block = np.ascontiguousarray(block)
+        if block.dtype != np.uint8 or block.size != self.n_chan * self.n_in * self.block_len:
+            raise ValueError("block must be uint8[n_chan][n_inputs][block_len]")
+        _ck(self._lib.corr_push_block_host(self._h, block.ctypes.data, _stream_handle(stream)),
+            "corr_push_block_host")
+
+    def dump_host(self, vis: np.ndarray | None = None, stokes: np.ndarray | None = None,
+                  want_stokes: bool | None = None, stream=None):
+        if want_stokes is None:
+            want_stokes = self.n_pol == 2
+        if vis is None:
+            vis = np.empty((self.n_chan, self.n_pairs, 2), dtype=np.int64)
+        if stokes is None and want_stokes:
+            stokes = np.empty((self.n_chan, self.n_apairs, 4, 2), dtype=np.int64)
+        _ck(self._lib.corr_dump_host(self._h, vis.ctypes.data,
+                                     stokes.ctypes.data if stokes is not None else None,
+                                     _stream_handle(stream)), "corr_dump_host")
+        return vis, stokes
+
+    # ---------------------------------------------------------------- misc
+    def check(self, stream=None):
+        _ck(self._lib.corr_check(self._h, _stream_handle(stream)), "corr_check")
+
+    def samples_integrated(self) -> int:
+        s = _ll()
+        _ck(self._lib.corr_sizes(self._h, None, None, ctypes.byref(s)), "corr_sizes")
+        return s.value
+
+    def launch_count(self) -> int:
+        return int(self._lib.corr_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.corr_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,76 @@
+// xe_internal.h -- structures shared by the host scheduler and the kernels.
+// Not part of the public ABI (include/corr.h is).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace xe {
+
+// Samples per pipeline chunk: one 128-byte row of fp16 (re, im) pairs, i.e.
+// exactly one 128B-swizzle atom along K.
+constexpr int kChunkSamples = 32;
+// Inputs per row tile: the MMA A operand stacks 64 inputs' real-part rows and
+// 64 inputs' imaginary-part rows (M = 128).
+constexpr int kTileInputs = 64;
+constexpr int kTmemCols = 512;
+constexpr int kMaxSegs = 8;
+constexpr int kMaxZRows = 512;
+constexpr int kPackedRowBytes = kChunkSamples;  // one byte per complex sample
+constexpr int kThreads = 320;                   // 10 warps, see xengine.cu
+
+// A contiguous range of inputs staged into the operand buffer ("Z") every
+// chunk.  Interleaved regions store, per group of 8 inputs, 8 rows of
+// [re, im] pairs (the "A rows") followed by 8 rows of [im, -re] pairs (the
+// "Q rows"); plain regions store A rows only.
+struct XRegion {
+  int in_lo;        // first input
+  int n_in;         // inputs staged (multiple of 64; rows past N read as zero)
+  int interleaved;  // 1: A and Q rows, 0: A rows only
+  int z_row;        // first row in the Z stage buffer (multiple of 8)
+  int pk_off;       // byte offset in the packed stage buffer
+};
+
+// One MMA stream of the unit: D[128 x n] += A(tile) * B(cols)^T into TMEM.
+struct XSeg {
+  int a_zrow;    // Z row of the 128-row A operand (64 inputs, interleaved)
+  int b_zrow;    // Z row of the first B row
+  int b_sbo;     // byte stride between 8-row groups of B (2048 interleaved, 1024 plain)
+  int n;         // B rows = output columns (multiple of 16, <= 256)
+  int tmem_col;  // first TMEM column of the accumulator
+  int row_in0;   // input index of the tile's first row
+  int col_in0;   // input index of the first column
+};
+
+struct XUnit {
+  int n_reg, n_seg;
+  int z_rows;    // rows staged per chunk (sum over regions)
+  int pk_bytes;  // packed bytes per chunk (sum over regions)
+  int work;      // relative MMA work (sum of n), for ordering
+  XRegion reg[2];
+  XSeg seg[kMaxSegs];
+};
+
+struct XParams {
+  const XUnit *units;  // [n_tpl], heaviest first
+  int n_tpl;
+  int n_chan;
+  int n_in;
+  int n_chunks;        // ceil(block_len / kChunkSamples) * blocks_per_launch
+  long long n_pairs;   // N(N+1)/2
+  int64_t *acc;        // [n_chan][n_pairs][2]
+  int *status;         // device status word (bit 0: a wait timed out)
+  unsigned long long timeout_ns;
+  int z_stages, pk_stages;
+  uint32_t z_stage_bytes, pk_stage_bytes;
+};
+
+// Host-side launchers (defined in the .cu files).
+cudaError_t launch_cmac(const void *tmap /* CUtensorMap, 64 B */, const XParams &p, int grid,
+                        int smem_bytes, cudaStream_t stream);
+cudaError_t cmac_set_smem(int smem_bytes);
+cudaError_t launch_dump(int64_t *acc, int64_t *vis, int64_t *stokes, int n_ant, int n_pol,
+                        int n_chan, cudaStream_t stream, int grid);
+cudaError_t launch_pitch(const uint8_t *src, uint8_t *dst, long long rows, int T, int pitch,
+                         cudaStream_t stream, int grid);
+
+}  // namespace xe

@@ -1,0 +1,325 @@
+// xengine.cu -- the X-engine CMAC kernel for sm_103a (tcgen05 + TMA + TMEM).
+//
+// For one channel, the X-engine (Sec. 2.3) forms V[i][j] = sum_t x_i conj(x_j)
+// over the lower triangle (Eq. 1, Eq. 2).  With x = a + j b:
+//   Re V_ij = sum_t a_i a_j + b_i b_j   = <[a_i, b_i], [a_j, b_j]>
+//   Im V_ij = sum_t b_i a_j - a_i b_j   = <[b_i, -a_i], [a_j, b_j]>
+// so with K running over (t, re/im) the whole channel is one real matrix
+// product D = Arows * Brows^T, where every input contributes an "A row"
+// [a, b] (used on both sides) and a "Q row" [b, -a] (row side only).  That is
+// a dense rank-2T update, so it runs on the tensor cores: fp16 operands (every
+// value in [-8, 8] is exact in fp16) and fp32 accumulators in TMEM.  Each
+// product is an integer of magnitude <= 64 and each block's partial sums stay
+// below 128 * block_len < 2^24, so every fp32 accumulation is exact; the
+// partials are folded into the int64 integration buffer once per block.
+//
+// Kernel structure (persistent, one CTA per SM, 10 warps):
+//   warp 8      TMA producer: packed bytes [channel][input][time] -> smem ring
+//   warps 0-3   unpack: 4-bit nibbles -> fp16 A/Q rows in the 128B-swizzled
+//               K-major layout the MMA reads (the paper's CPU "fluff" step,
+//               Sec. 2.3, moved on chip)
+//   warp 9      MMA issuer: tcgen05.mma M=128 (64 inputs' A rows + Q rows),
+//               N = columns of the triangle strip, K = 16 per instruction
+//   warps 4-7   epilogue: tcgen05.ld of the fp32 accumulators, exchange of
+//               re/im between lanes, int64 read-modify-write of the lower
+//               triangle in HBM
+// A work unit is (channel, template); a template names the inputs staged
+// per chunk and the MMAs (row tile x column range) that cover its part of
+// the triangle.  All waits are bounded by a timeout; on expiry the kernel
+// drains its own copies and MMAs, frees TMEM and reports through *status.
+#include <cuda.h>
+
+#include "ptx.cuh"
+#include "xe_internal.h"
+
+namespace xe {
+
+namespace {
+
+// sub.f16x2 on raw bit patterns (exact here: small integers only).
+__device__ __forceinline__ uint32_t hsub2_bits(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// Four packed samples (bytes of w, earliest in the low byte) -> the 16-byte
+// A-row chunk [a0 b0 a1 b1 a2 b2 a3 b3] and Q-row chunk [b0 -a0 b1 -a1 ...]
+// in fp16.  A nibble n encodes n - 16*(n >= 8); (n ^ 8) = value + 8, and
+// fp16 0x6400 | k is 1024 + k, so subtracting 1032 leaves the value.
+__device__ __forceinline__ void decode_word(uint32_t w, uint4 &a, uint4 &q) {
+  const uint32_t x = w ^ 0x88888888u;
+  const uint32_t lo = x & 0x0F0F0F0Fu;         // imaginary + 8, per byte
+  const uint32_t hi = (x >> 4) & 0x0F0F0F0Fu;  // real + 8, per byte
+  const uint32_t bias = 0x64086408u;           // fp16 (1032, 1032)
+  uint32_t r0 = (__byte_perm(hi, lo, 0x4400) & 0x00FF00FFu) | 0x64006400u;
+  uint32_t r1 = (__byte_perm(hi, lo, 0x5511) & 0x00FF00FFu) | 0x64006400u;
+  uint32_t r2 = (__byte_perm(hi, lo, 0x6622) & 0x00FF00FFu) | 0x64006400u;
+  uint32_t r3 = (__byte_perm(hi, lo, 0x7733) & 0x00FF00FFu) | 0x64006400u;
+  r0 = hsub2_bits(r0, bias);
+  r1 = hsub2_bits(r1, bias);
+  r2 = hsub2_bits(r2, bias);
+  r3 = hsub2_bits(r3, bias);
+  a = make_uint4(r0, r1, r2, r3);
+  // swap halves -> (b, a), flip the sign of the upper half -> (b, -a)
+  q = make_uint4(__byte_perm(r0, 0, 0x1032) ^ 0x80000000u, __byte_perm(r1, 0, 0x1032) ^ 0x80000000u,
+                 __byte_perm(r2, 0, 0x1032) ^ 0x80000000u, __byte_perm(r3, 0, 0x1032) ^ 0x80000000u);
+}
+
+struct Bars {
+  uint32_t pk_full, pk_empty, z_full, z_empty, acc_full, acc_empty, drain;
+};
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads, 1)
+    xengine_cmac_kernel(const __grid_constant__ CUtensorMap tmap, const XParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  // 1024-byte alignment for the swizzled operand atoms
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t *z_buf = smem;
+  uint8_t *pk_buf = z_buf + (size_t)p.z_stages * p.z_stage_bytes;
+  uint64_t *bar_mem = reinterpret_cast<uint64_t *>(pk_buf + (size_t)p.pk_stages * p.pk_stage_bytes);
+  // [pk_full x S][pk_empty x S][z_full x Z][z_empty x Z][acc_full][acc_empty][drain]
+  uint32_t *misc = reinterpret_cast<uint32_t *>(bar_mem + 2 * p.pk_stages + 2 * p.z_stages + 3);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(misc + 1);
+  const uint32_t bar0 = smem_u32(bar_mem);
+  Bars b;
+  b.pk_full = bar0;
+  b.pk_empty = bar0 + 8 * p.pk_stages;
+  b.z_full = bar0 + 16 * p.pk_stages;
+  b.z_empty = b.z_full + 8 * p.z_stages;
+  b.acc_full = b.z_empty + 8 * p.z_stages;
+  b.acc_empty = b.acc_full + 8;
+  b.drain = b.acc_empty + 8;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.pk_stages; ++s) {
+      mbar_init(b.pk_full + 8 * s, 1);
+      mbar_init(b.pk_empty + 8 * s, 4);
+    }
+    for (int s = 0; s < p.z_stages; ++s) {
+      mbar_init(b.z_full + 8 * s, 4);
+      mbar_init(b.z_empty + 8 * s, 1);
+    }
+    mbar_init(b.acc_full, 1);
+    mbar_init(b.acc_empty, 4);
+    mbar_init(b.drain, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 9) {
+    tmem_alloc(smem_u32(misc), kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = misc[0];
+
+  const long long n_work = (long long)p.n_tpl * p.n_chan;
+  const uint64_t to = p.timeout_ns;
+
+  if (warp == 8) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      prefetch_tmap(&tmap);
+      int s = 0;
+      uint32_t ph = 0;
+      int armed[8];
+      uint32_t armed_ph[8];
+      for (int k = 0; k < 8; ++k) armed[k] = 0, armed_ph[k] = 0;
+      bool ok = true;
+      for (long long w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+        const int tpl = (int)(w / p.n_chan), c = (int)(w % p.n_chan);
+        const XUnit *u = p.units + tpl;
+        const int n_reg = u->n_reg;
+        const uint32_t bytes = (uint32_t)u->pk_bytes;
+        for (int k = 0; k < p.n_chunks; ++k) {
+          if (!mbar_wait(b.pk_empty + 8 * s, ph ^ 1u, abort_flag, to)) { ok = false; break; }
+          const uint32_t full = b.pk_full + 8 * s;
+          mbar_arrive_expect_tx(full, bytes);
+          armed[s] = 1;
+          armed_ph[s] = ph;
+          const uint32_t dst0 = smem_u32(pk_buf + (size_t)s * p.pk_stage_bytes);
+          for (int r = 0; r < n_reg; ++r) {
+            const int in_lo = u->reg[r].in_lo, n_in = u->reg[r].n_in, off = u->reg[r].pk_off;
+            for (int bx = 0; bx < n_in; bx += kTileInputs)
+              tma_load_3d(dst0 + off + bx * kPackedRowBytes, &tmap, full, k * kChunkSamples,
+                          in_lo + bx, c);
+          }
+          if (++s == p.pk_stages) { s = 0; ph ^= 1u; }
+        }
+      }
+      // every load this thread armed must have landed before the CTA exits
+      int dummy = 0;
+      for (int k = 0; k < p.pk_stages; ++k)
+        if (armed[k]) mbar_wait(b.pk_full + 8 * k, armed_ph[k], &dummy, to);
+    }
+  } else if (warp == 9) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int zs = 0;
+      uint32_t zph = 0;
+      long long nu = 0;
+      bool ok = true;
+      for (long long w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++nu) {
+        const XUnit *u = p.units + (int)(w / p.n_chan);
+        const int n_seg = u->n_seg;
+        if (nu > 0 && !mbar_wait(b.acc_empty, (uint32_t)((nu - 1) & 1), abort_flag, to)) break;
+        tc_fence_after();
+        for (int k = 0; k < p.n_chunks; ++k) {
+          if (!mbar_wait(b.z_full + 8 * zs, zph, abort_flag, to)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t zb = smem_u32(z_buf + (size_t)zs * p.z_stage_bytes);
+          for (int sg = 0; sg < n_seg; ++sg) {
+            const XSeg sgm = u->seg[sg];
+            const uint32_t idesc = idesc_f16_f32(128, sgm.n);
+            const uint32_t a0 = zb + (uint32_t)sgm.a_zrow * 128u;
+            const uint32_t b0 = zb + (uint32_t)sgm.b_zrow * 128u;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t da = sdesc_sw128(a0 + 32u * kk, 1024u);
+              const uint64_t db = sdesc_sw128(b0 + 32u * kk, (uint32_t)sgm.b_sbo);
+              mma_f16_ss(tmem + (uint32_t)sgm.tmem_col, da, db, idesc, (k | kk) != 0);
+            }
+          }
+          mma_commit(b.z_empty + 8 * zs);
+          if (++zs == p.z_stages) { zs = 0; zph ^= 1u; }
+        }
+        if (ok) mma_commit(b.acc_full);
+      }
+      // all MMAs this thread issued complete before TMEM is released
+      mma_commit(b.drain);
+      int dummy = 0;
+      mbar_wait(b.drain, 0, &dummy, to);
+    }
+  } else if (warp < 4) {
+    // ------------------------------------------------------------ unpack
+    const int tid = threadIdx.x;  // 0..127
+    int s = 0, zs = 0;
+    uint32_t ph = 0, zph = 0;
+    bool ok = true;
+    for (long long w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+      const XUnit *u = p.units + (int)(w / p.n_chan);
+      const int n_reg = u->n_reg;
+      for (int k = 0; k < p.n_chunks; ++k) {
+        if (!mbar_wait(b.pk_full + 8 * s, ph, abort_flag, to)) { ok = false; break; }
+        if (!mbar_wait(b.z_empty + 8 * zs, zph ^ 1u, abort_flag, to)) { ok = false; break; }
+        const uint8_t *pk = pk_buf + (size_t)s * p.pk_stage_bytes;
+        uint8_t *zst = z_buf + (size_t)zs * p.z_stage_bytes;
+        for (int r = 0; r < n_reg; ++r) {
+          const XRegion rg = u->reg[r];
+          const uint8_t *pkr = pk + rg.pk_off;
+          uint8_t *zr = zst + (size_t)rg.z_row * 128;
+          const int items = rg.n_in * 2;
+          for (int it = tid; it < items; it += 128) {
+            const int row = it >> 1, h = it & 1;
+            const uint4 in = *reinterpret_cast<const uint4 *>(pkr + row * 32 + h * 16);
+            const int rho = rg.interleaved ? (((row >> 3) << 4) | (row & 7)) : row;
+            uint8_t *pa = zr + (size_t)rho * 128;
+            uint8_t *pq = pa + 8 * 128;
+            const int sw = row & 7;
+            const uint32_t wv[4] = {in.x, in.y, in.z, in.w};
+#pragma unroll
+            for (int wi = 0; wi < 4; ++wi) {
+              uint4 va, vq;
+              decode_word(wv[wi], va, vq);
+              const int off = ((4 * h + wi) ^ sw) << 4;
+              *reinterpret_cast<uint4 *>(pa + off) = va;
+              if (rg.interleaved) *reinterpret_cast<uint4 *>(pq + off) = vq;
+            }
+          }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(b.z_full + 8 * zs);
+          mbar_arrive(b.pk_empty + 8 * s);
+        }
+        if (++s == p.pk_stages) { s = 0; ph ^= 1u; }
+        if (++zs == p.z_stages) { zs = 0; zph ^= 1u; }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    const int rho = 32 * q + lane;
+    const int g = rho >> 4, is_im = (rho >> 3) & 1, l = rho & 7;
+    long long nu = 0;
+    for (long long w = blockIdx.x; w < n_work; w += gridDim.x, ++nu) {
+      const int tpl = (int)(w / p.n_chan), c = (int)(w % p.n_chan);
+      const XUnit *u = p.units + tpl;
+      if (!mbar_wait(b.acc_full, (uint32_t)(nu & 1), abort_flag, to)) break;
+      tc_fence_after();
+      const int n_seg = u->n_seg;
+      for (int sg = 0; sg < n_seg; ++sg) {
+        const XSeg sgm = u->seg[sg];
+        const int i = sgm.row_in0 + 8 * g + l;
+        const bool row_ok = i < p.n_in;
+        int64_t *arow = p.acc + ((long long)c * p.n_pairs + (long long)i * (i + 1) / 2) * 2;
+        for (int cb = 0; cb < sgm.n; cb += 16) {
+          uint32_t v[16];
+          __syncwarp();
+          tmem_ld_32x32b_x16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(sgm.tmem_col + cb), v);
+          tmem_ld_wait();
+          int re[8], im[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const uint32_t send = is_im ? v[e] : v[8 + e];
+            const uint32_t got = __shfl_xor_sync(0xffffffffu, send, 8);
+            const int mine = __float2int_rn(__uint_as_float(is_im ? v[8 + e] : v[e]));
+            const int other = __float2int_rn(__uint_as_float(got));
+            re[e] = is_im ? other : mine;
+            im[e] = is_im ? mine : other;
+          }
+          const int j0 = sgm.col_in0 + cb + (is_im ? 8 : 0);
+          const int nvalid = row_ok ? min(8, i - j0 + 1) : 0;
+          if (nvalid > 0) {
+            longlong2 *ptr = reinterpret_cast<longlong2 *>(arow + 2 * (long long)j0);
+            longlong2 old[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              if (e < nvalid) old[e] = ptr[e];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              if (e < nvalid) {
+                old[e].x += re[e];
+                old[e].y += im[e];
+                ptr[e] = old[e];
+              }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b.acc_empty);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 9) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(p.status, 1);
+}
+
+cudaError_t cmac_set_smem(int smem_bytes) {
+  return cudaFuncSetAttribute(xengine_cmac_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_bytes);
+}
+
+cudaError_t launch_cmac(const void *tmap, const XParams &p, int grid, int smem_bytes,
+                        cudaStream_t stream) {
+  CUtensorMap m = *reinterpret_cast<const CUtensorMap *>(tmap);
+  xengine_cmac_kernel<<<grid, kThreads, smem_bytes, stream>>>(m, p);
+  return cudaGetLastError();
+}
+
+}  // namespace xe

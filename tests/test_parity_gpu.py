@@ -1,0 +1,241 @@
+"""Parity of the CUDA X-engine with the CPU oracle, through the C ABI.
+
+Integer arithmetic end to end: every comparison is exact (bit-for-bit int64
+visibilities and Stokes products); no tolerance applies anywhere.
+"""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+N_THREADS = max(1, min(os.cpu_count() or 1, 64))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def corr(torch_cuda):
+    from paper_2406_19013_gb300 import build
+    build.build()
+    from paper_2406_19013_gb300 import corr as c
+    return c
+
+
+def _run(corr, torch, blocks, n_ant, n_pol, want_stokes=True):
+    C, N, T = blocks[0].shape
+    with corr.Correlator(n_ant, n_pol, C, T) as xc:
+        for b in blocks:
+            xc.push_block(torch.from_numpy(b).cuda())
+        vis, st = xc.dump(want_stokes=want_stokes and n_pol == 2)
+        xc.check()
+        assert xc.samples_integrated() == 0
+        return vis.cpu().numpy(), (st.cpu().numpy() if st is not None else None)
+
+
+def _oracle(oracle_mod, blocks, n_ant, n_pol):
+    vis = None
+    for b in blocks:
+        vis = oracle_mod.xcorr(b, vis=vis, n_threads=N_THREADS)
+    st = oracle_mod.stokes(vis, n_ant) if n_pol == 2 else None
+    return vis, st
+
+
+def test_tiny_workload(corr, torch_cuda, oracle_mod, synth_mod):
+    # 8 dual-pol antennas, 64 channels, 2048 samples, noise + tone
+    w = synth_mod.workload("tiny")
+    x = w.block(0)
+    vis, st = _run(corr, torch_cuda, [x], w.n_ant, w.n_pol)
+    ov, ost = _oracle(oracle_mod, [x], w.n_ant, w.n_pol)
+    assert np.array_equal(vis, ov)
+    assert np.array_equal(st, ost)
+
+
+@pytest.mark.parametrize("n_ant,n_pol,C,T,nb", [
+    (1, 1, 3, 16, 1),        # one input
+    (33, 1, 4, 48, 3),       # ragged N, T not a multiple of the 32-sample chunk
+    (64, 2, 3, 4096, 1),     # N = 128: two full row tiles
+    (96, 2, 7, 8192, 2),     # the paper's 192 inputs, few channels
+    (100, 2, 5, 1000, 2),    # N = 200: two units; T % 16 != 0 (pitched staging)
+    (128, 2, 2, 512, 1),     # N = 256: largest single window
+    (150, 2, 3, 512, 1),     # N = 300: row-tile pairs against 256-column pieces
+    (320, 2, 2, 256, 1),     # N = 640: off-diagonal pieces
+    (17, 2, 9, 2056, 1),     # N = 34, T % 32 = 8
+])
+def test_ragged_shapes(corr, torch_cuda, oracle_mod, synth_mod, n_ant, n_pol, C, T, nb):
+    N = n_ant * n_pol
+    tones = synth_mod.random_phase_tone(N, 5)
+    blocks = [synth_mod.make_block(N, C, T, seed=100 + N, block=b, tones=tones) for b in range(nb)]
+    vis, st = _run(corr, torch_cuda, blocks, n_ant, n_pol)
+    ov, ost = _oracle(oracle_mod, blocks, n_ant, n_pol)
+    assert np.array_equal(vis, ov)
+    if n_pol == 2:
+        assert np.array_equal(st, ost)
+
+
+def test_extremes_at_max_block_len(corr, torch_cuda, oracle_mod, synth_mod):
+    # The largest block keeps every fp32 partial an exact integer: -8-8j on
+    # every sample gives autos of 128 * 131071 = 16777088 (< 2^24).  The
+    # second block adds small values after a large running sum, which an
+    # accumulator that dropped low-order bits would lose.
+    T = 131071
+    n_ant, C = 8, 2
+    N = 2 * n_ant
+    x0 = np.full((C, N, T), 0x88, dtype=np.uint8)
+    rng = np.random.default_rng(3)
+    re = rng.integers(-8, 8, size=(C, N, T))
+    im = rng.integers(-8, 8, size=(C, N, T))
+    x1 = synth_mod.pack(re, im)
+    x1[:, :, : 3 * T // 4] = 0x88
+    small = rng.integers(-1, 2, size=(C, N, T // 4))
+    x1[:, :, 3 * T // 4: 3 * T // 4 + T // 4] = synth_mod.pack(small, -small)
+    for blocks in ([x0], [x1], [x0, x1]):
+        vis, st = _run(corr, torch_cuda, blocks, n_ant, 2)
+        ov, ost = _oracle(oracle_mod, blocks, n_ant, 2)
+        assert np.array_equal(vis, ov)
+        assert np.array_equal(st, ost)
+        if len(blocks) == 1 and blocks[0] is x0:
+            assert (vis[..., 0] == 128 * T).all() and not vis[..., 1].any()
+
+
+def test_all_byte_values(corr, torch_cuda, oracle_mod):
+    # every byte value against every other, 16 inputs x 256 samples
+    N, T = 16, 256
+    x = np.empty((2, N, T), dtype=np.uint8)
+    for i in range(N):
+        x[0, i] = (np.arange(T) * (2 * i + 1) + i) % 256
+        x[1, i] = (np.arange(T) * 7 + 31 * i) % 256
+    vis, st = _run(corr, torch_cuda, [x], 8, 2)
+    ov, ost = _oracle(oracle_mod, [x], 8, 2)
+    assert np.array_equal(vis, ov)
+    assert np.array_equal(st, ost)
+
+
+def test_dump_semantics(corr, torch_cuda, oracle_mod, synth_mod):
+    torch = torch_cuda
+    n_ant, C, T = 12, 6, 320
+    N = 2 * n_ant
+    b0 = synth_mod.make_block(N, C, T, seed=1, block=0)
+    b1 = synth_mod.make_block(N, C, T, seed=1, block=1)
+    with corr.Correlator(n_ant, 2, C, T) as xc:
+        xc.push_block(torch.from_numpy(b0).cuda())
+        assert xc.samples_integrated() == T
+        v0, _ = xc.dump(want_stokes=False)
+        assert np.array_equal(v0.cpu().numpy(), oracle_mod.xcorr(b0))
+        # the integration restarted at zero
+        v, s = xc.dump()
+        assert not v.cpu().numpy().any() and not s.cpu().numpy().any()
+        # blocks accumulate; a dump with no outputs still resets
+        xc.push_block(torch.from_numpy(b0).cuda())
+        xc.push_block(torch.from_numpy(b1).cuda())
+        assert xc.samples_integrated() == 2 * T
+        _, s01 = xc.dump(want_vis=False)
+        ov = oracle_mod.xcorr(b1, vis=oracle_mod.xcorr(b0))
+        assert np.array_equal(s01.cpu().numpy(), oracle_mod.stokes(ov, n_ant))
+        xc.push_block(torch.from_numpy(b1).cuda())
+        xc.dump(want_vis=False, want_stokes=False)
+        v, _ = xc.dump(want_stokes=False)
+        assert not v.cpu().numpy().any()
+        xc.check()
+    with corr.Correlator(N, 1, C, T) as xs:
+        xs.push_block(torch.from_numpy(b0).cuda())
+        with pytest.raises(corr.CorrError) as e:
+            xs.dump(want_stokes=True)
+        assert e.value.code == corr.CORR_EINVAL
+        v, s = xs.dump()
+        assert s is None and np.array_equal(v.cpu().numpy(), oracle_mod.xcorr(b0))
+
+
+def test_host_buffer_api(corr, torch_cuda, oracle_mod, synth_mod):
+    w = synth_mod.workload("tiny")
+    blocks = [w.block(b) for b in range(3)]
+    with corr.Correlator(w.n_ant, w.n_pol, w.n_chan, w.block_len) as xc:
+        for b in blocks:
+            xc.push_block_host(b)
+        vis, st = xc.dump_host()
+        xc.check()
+    ov, ost = _oracle(oracle_mod, blocks, w.n_ant, w.n_pol)
+    assert np.array_equal(vis, ov)
+    assert np.array_equal(st, ost)
+
+
+def test_independent_contexts(corr, torch_cuda, oracle_mod, synth_mod):
+    torch = torch_cuda
+    xa = synth_mod.make_block(40, 3, 256, seed=2)
+    xb = synth_mod.make_block(10, 5, 96, seed=3)
+    a = corr.Correlator(20, 2, 3, 256)
+    b = corr.Correlator(10, 1, 5, 96)
+    try:
+        a.push_block(torch.from_numpy(xa).cuda())
+        b.push_block(torch.from_numpy(xb).cuda())
+        a.push_block(torch.from_numpy(xa).cuda())
+        va, _ = a.dump()
+        vb, _ = b.dump()
+        assert np.array_equal(va.cpu().numpy(), 2 * oracle_mod.xcorr(xa))
+        assert np.array_equal(vb.cpu().numpy(), oracle_mod.xcorr(xb))
+    finally:
+        a.close()
+        b.close()
+
+
+def _autos_numpy(x):
+    s = x.astype(np.int8)
+    re = (s >> 4).astype(np.int64)
+    im = ((x << 4).astype(np.uint8).astype(np.int8) >> 4).astype(np.int64)
+    return (re * re + im * im).sum(axis=2)
+
+
+def test_paper_scale_sampled(corr, torch_cuda, oracle_mod, synth_mod):
+    # 96 dual-pol antennas, 1024 channels, 8192-sample blocks: the launch the
+    # benchmark times.  Whole channels and random pairs against the oracle,
+    # and every auto-correlation of every channel against numpy.
+    torch = torch_cuda
+    w = synth_mod.workload("paper")
+    x = w.block(0)
+    with corr.Correlator(w.n_ant, w.n_pol, w.n_chan, w.block_len) as xc:
+        xc.push_block(torch.from_numpy(x).cuda())
+        vis, st = xc.dump()
+        xc.check()
+    vis = vis.cpu().numpy()
+    st = st.cpu().numpy()
+    chans = [0, 1, 511, 1023]
+    ov = oracle_mod.xcorr(np.ascontiguousarray(x[chans]), n_threads=N_THREADS)
+    assert np.array_equal(vis[chans], ov)
+    assert np.array_equal(st[chans], oracle_mod.stokes(ov, w.n_ant))
+    rng = np.random.default_rng(0)
+    for _ in range(64):
+        c = int(rng.integers(0, w.n_chan))
+        i = int(rng.integers(0, w.n_in))
+        j = int(rng.integers(0, i + 1))
+        assert tuple(vis[c, i * (i + 1) // 2 + j]) == oracle_mod.xcorr_pair(x, c, i, j)
+    autos = _autos_numpy(x)
+    diag = np.arange(w.n_in) * (np.arange(w.n_in) + 3) // 2
+    assert np.array_equal(vis[:, diag, 0], autos)
+    assert not vis[:, diag, 1].any()
+
+
+def test_large_n_sampled(corr, torch_cuda, oracle_mod, synth_mod):
+    # 1024 dual-pol antennas (2048 inputs), 2 channels of 4096 samples
+    torch = torch_cuda
+    w = synth_mod.workload("large_n")
+    x = w.block(0, c0=0, n_chan=2)
+    with corr.Correlator(w.n_ant, w.n_pol, 2, w.block_len) as xc:
+        xc.push_block(torch.from_numpy(x).cuda())
+        vis, _ = xc.dump(want_stokes=False)
+        xc.check()
+    vis = vis.cpu().numpy()
+    rng = np.random.default_rng(1)
+    for c in range(2):
+        for i in [0, 63, 64, 255, 256, 257, 1000, 2047]:
+            for j in sorted(set([0, i // 2, max(0, i - 1), i] + list(rng.integers(0, i + 1, 4)))):
+                assert tuple(vis[c, i * (i + 1) // 2 + j]) == oracle_mod.xcorr_pair(x, c, i, int(j))
+    autos = _autos_numpy(x)
+    diag = np.arange(w.n_in) * (np.arange(w.n_in) + 3) // 2
+    assert np.array_equal(vis[:, diag, 0], autos)
