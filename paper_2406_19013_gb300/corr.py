@@ -146,24 +146,37 @@ class Correlator:
         return vis, stokes
 
     # ---------------------------------------------------------------- host
-    def push_block_host(self, block: np.ndarray, stream=None):
-        block = np.ascontiguousarray(block)
-        if block.dtype != np.uint8 or block.size != self.n_chan * self.n_in * self.block_len:
-            raise ValueError("block must be uint8[n_chan][n_inputs][block_len]")
-        _ck(self._lib.corr_push_block_host(self._h, block.ctypes.data, _stream_handle(stream)),
+    @staticmethod
+    def _host_ptr(a, dtype, n, what):
+        """Address of a contiguous host buffer (numpy array or CPU torch tensor)."""
+        if isinstance(a, np.ndarray):
+            if a.dtype != dtype or a.size != n or not a.flags.c_contiguous:
+                raise ValueError(f"{what} must be a contiguous {np.dtype(dtype).name}[{n}] array")
+            return a.ctypes.data
+        if a.device.type != "cpu" or not a.is_contiguous() or a.numel() != n or \
+                a.element_size() != np.dtype(dtype).itemsize:
+            raise ValueError(f"{what} must be a contiguous host tensor of {n} elements")
+        return a.data_ptr()
+
+    def push_block_host(self, block, stream=None):
+        """block: uint8[n_chan][n_inputs][block_len] numpy array or CPU tensor (pinned is faster)."""
+        if isinstance(block, np.ndarray):
+            block = np.ascontiguousarray(block)
+        ptr = self._host_ptr(block, np.uint8, self.n_chan * self.n_in * self.block_len, "block")
+        _ck(self._lib.corr_push_block_host(self._h, ptr, _stream_handle(stream)),
             "corr_push_block_host")
 
-    def dump_host(self, vis: np.ndarray | None = None, stokes: np.ndarray | None = None,
-                  want_stokes: bool | None = None, stream=None):
+    def dump_host(self, vis=None, stokes=None, want_stokes: bool | None = None, stream=None):
         if want_stokes is None:
-            want_stokes = self.n_pol == 2
+            want_stokes = self.n_pol == 2 or stokes is not None
         if vis is None:
             vis = np.empty((self.n_chan, self.n_pairs, 2), dtype=np.int64)
         if stokes is None and want_stokes:
             stokes = np.empty((self.n_chan, self.n_apairs, 4, 2), dtype=np.int64)
-        _ck(self._lib.corr_dump_host(self._h, vis.ctypes.data,
-                                     stokes.ctypes.data if stokes is not None else None,
-                                     _stream_handle(stream)), "corr_dump_host")
+        pv = self._host_ptr(vis, np.int64, self.n_chan * self.n_pairs * 2, "vis")
+        ps = (self._host_ptr(stokes, np.int64, self.n_chan * self.n_apairs * 8, "stokes")
+              if stokes is not None else None)
+        _ck(self._lib.corr_dump_host(self._h, pv, ps, _stream_handle(stream)), "corr_dump_host")
         return vis, stokes
 
     # ---------------------------------------------------------------- misc
