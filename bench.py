@@ -222,18 +222,24 @@ def run_ours(args):
     vis = torch.empty((N_CHAN, N_PAIRS, 2), dtype=torch.int64, device=dev)
     st = torch.empty((N_CHAN, N_APAIRS, 4, 2), dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream()
+    # the step pushes its 64 blocks in groups; each group is one CMAC launch
+    # that integrates GROUP blocks before its int64 fold
+    group = max(1, min(args.group, BLOCKS_PER_STEP))
+    n_groups = -(-BLOCKS_PER_STEP // group)
     # one event pair around every CMAC launch of the timed steps
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(BLOCKS_PER_STEP)] for _ in range(args.steps)]
+           for _ in range(n_groups)] for _ in range(args.steps)]
 
     def step(s, record):
-        for b in range(BLOCKS_PER_STEP):
-            blk = ring[(s * BLOCKS_PER_STEP + b) % ring_n]
+        for gi in range(n_groups):
+            b0 = gi * group
+            blks = [ring[(s * BLOCKS_PER_STEP + b) % ring_n]
+                    for b in range(b0, min(b0 + group, BLOCKS_PER_STEP))]
             if record:
-                ev[s][b][0].record(stream)
-            xc.push_block(blk, stream)
+                ev[s][gi][0].record(stream)
+            xc.push_blocks(blks, stream)
             if record:
-                ev[s][b][1].record(stream)
+                ev[s][gi][1].record(stream)
         xc.dump(vis, st, stream=stream)
 
     def barrier():
@@ -274,9 +280,11 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (the CMAC launch)
     launch_avg_ms = sum(launch_ms) / len(launch_ms)
-    useful_tflop = CMAC_PER_BLOCK * OPS_PER_CMAC / 1e12
+    blocks_per_launch = BLOCKS_PER_STEP / n_groups
+    useful_tflop = CMAC_PER_BLOCK * blocks_per_launch * OPS_PER_CMAC / 1e12
     _, issued_cmac_per_chan_sample, _ = plan(N_IN)
-    issued_tflop = issued_cmac_per_chan_sample * N_CHAN * BLOCK_LEN * OPS_PER_CMAC / 1e12
+    issued_tflop = (issued_cmac_per_chan_sample * N_CHAN * BLOCK_LEN * blocks_per_launch *
+                    OPS_PER_CMAC / 1e12)
     peak, peak_kind = peaks()
     achieved = useful_tflop / (launch_avg_ms / 1e3)
     roofline = {
@@ -287,6 +295,7 @@ def run_ours(args):
         "issued_frac": issued_tflop / (launch_avg_ms / 1e3) / peak,
         "useful_over_issued": useful_tflop / issued_tflop,
         "algorithmic_flop_per_launch": useful_tflop * 1e12,
+        "blocks_per_launch": blocks_per_launch,
     }
 
     # ---- end to end through the host-buffer C-ABI calls
@@ -360,6 +369,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ring", type=int, default=2, help="distinct device-resident blocks")
+    ap.add_argument("--group", type=int, default=8, help="blocks per corr_push_blocks call")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-channels", type=int, default=16)
     ap.add_argument("--n-chan", type=int, default=N_CHAN,

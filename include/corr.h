@@ -93,6 +93,17 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
 int corr_push_block(corr_ctx *ctx, const uint8_t *d_block, void *stream);
 
 /*
+ * Integrates n_blocks blocks (d_blocks: host array of n_blocks device
+ * pointers, each as for corr_push_block).  Equivalent to n_blocks calls of
+ * corr_push_block, but up to 8 blocks share one launch and one fold into the
+ * int64 buffer (fewer while 8 * block_len exceeds CORR_MAX_BLOCK_LEN).  The
+ * pointer array itself may be reused as soon as the call returns.
+ * Errors: CORR_EINVAL (NULL ctx or array, n_blocks < 1, a NULL or misaligned
+ * block pointer; nothing is enqueued), CORR_ECUDA.
+ */
+int corr_push_blocks(corr_ctx *ctx, const uint8_t *const *d_blocks, int n_blocks, void *stream);
+
+/*
  * Ends the integration: writes the visibilities accumulated since the last
  * dump to d_vis (int64[n_chan][P][2]) if it is not NULL, the full-Stokes
  * products to d_stokes (int64[n_chan][A][4][2]) if it is not NULL, and zeroes

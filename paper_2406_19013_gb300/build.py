@@ -19,7 +19,8 @@ LIB = os.path.join(HERE, "libcorr.so")
 SOURCES = ["xengine.cu", "dump.cu", "corr.cu"]
 HEADERS = ["ptx.cuh", "xe_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-I", INCLUDE]
 
 
 def _nvcc() -> str:

@@ -32,6 +32,7 @@ _vp, _ci, _ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
 ABI = [
     ("corr_create", _ci, [_ci, _ci, _ci, _ci, ctypes.POINTER(_vp)]),
     ("corr_push_block", _ci, [_vp, _vp, _vp]),
+    ("corr_push_blocks", _ci, [_vp, ctypes.POINTER(_vp), _ci, _vp]),
     ("corr_dump", _ci, [_vp, _vp, _vp, _vp]),
     ("corr_push_block_host", _ci, [_vp, _vp, _vp]),
     ("corr_dump_host", _ci, [_vp, _vp, _vp, _vp]),
@@ -129,6 +130,21 @@ class Correlator:
         else:
             ptr = int(block)
         _ck(self._lib.corr_push_block(self._h, ptr, _stream_handle(stream)), "corr_push_block")
+
+    def push_blocks(self, blocks, stream=None):
+        """Integrates several blocks (device tensors or pointers) with shared folds."""
+        ptrs = []
+        for blk in blocks:
+            if hasattr(blk, "data_ptr"):
+                if not (blk.is_cuda and blk.is_contiguous() and
+                        blk.numel() == self.n_chan * self.n_in * self.block_len):
+                    raise ValueError("each block must be a contiguous uint8 CUDA tensor of one block")
+                ptrs.append(blk.data_ptr())
+            else:
+                ptrs.append(int(blk))
+        arr = (_vp * max(1, len(ptrs)))(*ptrs)
+        _ck(self._lib.corr_push_blocks(self._h, arr, len(ptrs), _stream_handle(stream)),
+            "corr_push_blocks")
 
     def dump(self, vis=None, stokes=None, want_vis: bool = True, want_stokes: bool | None = None,
              stream=None):

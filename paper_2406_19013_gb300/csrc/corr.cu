@@ -10,7 +10,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/corr.h"
+#include "corr.h"
 #include "xe_internal.h"
 
 using xe::XParams;
@@ -253,6 +253,7 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
   ctx->pk_stage_bytes = (uint32_t)round_up(max_pk, 128);
   ctx->pk_stages = 4;
   const int fixed = 1024 /* alignment slack */ + 256 /* barriers, TMEM address, flags */;
+  static_assert(8 * (2 * 4 + 2 * 4 + 2 + xe::kMmaWarps) + 8 <= 256, "barrier area");
   int zs = (smem_optin - fixed - ctx->pk_stages * (int)ctx->pk_stage_bytes) / (int)ctx->z_stage_bytes;
   zs = std::min(zs, 4);
   if (zs < 2) {
@@ -297,28 +298,23 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
   return CORR_OK;
 }
 
-int corr_push_block(corr_ctx *ctx, const uint8_t *d_block, void *stream) {
-  if (!ctx || !d_block) return CORR_EINVAL;
-  if ((reinterpret_cast<uintptr_t>(d_block) & 15u) != 0) return CORR_EINVAL;
+int corr_push_blocks(corr_ctx *ctx, const uint8_t *const *d_blocks, int n_blocks,
+                     void *stream) {
+  if (!ctx || !d_blocks || n_blocks <= 0) return CORR_EINVAL;
+  for (int k = 0; k < n_blocks; ++k)
+    if (!d_blocks[k] || (reinterpret_cast<uintptr_t>(d_blocks[k]) & 15u) != 0) return CORR_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const uint8_t *src = d_block;
-  int rc;
-  if (ctx->d_pitched) {
-    if ((rc = cuda_err(xe::launch_pitch(d_block, ctx->d_pitched,
-                                        (long long)ctx->n_chan * ctx->n_in, ctx->block_len,
-                                        ctx->pitch, st, ctx->n_sm * 8))) != CORR_OK)
-      return rc;
-    ctx->launches++;
-    src = ctx->d_pitched;
-  }
-  alignas(64) CUtensorMap m;
-  if ((rc = encode_block_map(ctx, src, &m)) != CORR_OK) return rc;
+  static_assert(sizeof(CUtensorMap) == sizeof(xe::XMaps::m[0]), "tensor map size");
+  // a fold must come before 2^24 / 128 samples have been accumulated in fp32
+  int per = std::min(xe::kMaxBlocksPerLaunch, (CORR_MAX_BLOCK_LEN) / ctx->block_len);
+  if (ctx->d_pitched) per = 1;  // one pitched staging buffer
+  per = std::max(per, 1);
   XParams p;
   p.units = ctx->d_units;
   p.n_tpl = ctx->n_tpl;
   p.n_chan = ctx->n_chan;
   p.n_in = ctx->n_in;
-  p.n_chunks = (ctx->block_len + xe::kChunkSamples - 1) / xe::kChunkSamples;
+  p.chunks_per_block = (ctx->block_len + xe::kChunkSamples - 1) / xe::kChunkSamples;
   p.n_pairs = ctx->n_pairs;
   p.acc = ctx->d_acc;
   p.status = ctx->d_status;
@@ -329,10 +325,35 @@ int corr_push_block(corr_ctx *ctx, const uint8_t *d_block, void *stream) {
   p.pk_stage_bytes = ctx->pk_stage_bytes;
   const long long n_work = (long long)ctx->n_tpl * ctx->n_chan;
   const int grid = (int)std::min<long long>(n_work, ctx->n_sm);
-  if ((rc = cuda_err(xe::launch_cmac(&m, p, grid, ctx->smem_bytes, st))) != CORR_OK) return rc;
-  ctx->launches++;
-  ctx->samples += ctx->block_len;
+  int rc;
+  for (int k0 = 0; k0 < n_blocks; k0 += per) {
+    const int nb = std::min(per, n_blocks - k0);
+    xe::XMaps maps;
+    std::memset(&maps, 0, sizeof(maps));
+    for (int k = 0; k < nb; ++k) {
+      const uint8_t *src = d_blocks[k0 + k];
+      if (ctx->d_pitched) {
+        if ((rc = cuda_err(xe::launch_pitch(src, ctx->d_pitched, (long long)ctx->n_chan * ctx->n_in,
+                                            ctx->block_len, ctx->pitch, st, ctx->n_sm * 8))) !=
+            CORR_OK)
+          return rc;
+        ctx->launches++;
+        src = ctx->d_pitched;
+      }
+      if ((rc = encode_block_map(ctx, src, reinterpret_cast<CUtensorMap *>(maps.m[k]))) != CORR_OK)
+        return rc;
+    }
+    p.n_blocks = nb;
+    if ((rc = cuda_err(xe::launch_cmac(maps, p, grid, ctx->smem_bytes, st))) != CORR_OK) return rc;
+    ctx->launches++;
+    ctx->samples += (long long)nb * ctx->block_len;
+  }
   return CORR_OK;
+}
+
+int corr_push_block(corr_ctx *ctx, const uint8_t *d_block, void *stream) {
+  if (!ctx || !d_block) return CORR_EINVAL;
+  return corr_push_blocks(ctx, &d_block, 1, stream);
 }
 
 int corr_dump(corr_ctx *ctx, int64_t *d_vis, int64_t *d_stokes, void *stream) {

@@ -16,7 +16,17 @@ constexpr int kTmemCols = 512;
 constexpr int kMaxSegs = 8;
 constexpr int kMaxZRows = 512;
 constexpr int kPackedRowBytes = kChunkSamples;  // one byte per complex sample
-constexpr int kThreads = 320;                   // 10 warps, see xengine.cu
+// Warp roles (see xengine.cu): unpack, epilogue (one per TMEM lane quarter),
+// TMA producer, MMA issuers (one issue stream per accumulator).
+constexpr int kUnpackWarps = 8;
+constexpr int kEpiWarps = 4;
+constexpr int kMmaWarps = 4;
+constexpr int kWarpEpi0 = kUnpackWarps;
+constexpr int kWarpTma = kWarpEpi0 + kEpiWarps;
+constexpr int kWarpMma0 = kWarpTma + 1;
+constexpr int kThreads = 32 * (kWarpMma0 + kMmaWarps);
+// Blocks integrated by one launch before the fold into int64.
+constexpr int kMaxBlocksPerLaunch = 8;
 
 // A contiguous range of inputs staged into the operand buffer ("Z") every
 // chunk.  Interleaved regions store, per group of 8 inputs, 8 rows of
@@ -55,7 +65,8 @@ struct XParams {
   int n_tpl;
   int n_chan;
   int n_in;
-  int n_chunks;        // ceil(block_len / kChunkSamples) * blocks_per_launch
+  int chunks_per_block;  // ceil(block_len / kChunkSamples)
+  int n_blocks;          // blocks in this launch (<= kMaxBlocksPerLaunch)
   long long n_pairs;   // N(N+1)/2
   int64_t *acc;        // [n_chan][n_pairs][2]
   int *status;         // device status word (bit 0: a wait timed out)
@@ -64,9 +75,14 @@ struct XParams {
   uint32_t z_stage_bytes, pk_stage_bytes;
 };
 
+// One TMA descriptor (CUtensorMap, 128 bytes) per block of the launch.
+struct XMaps {
+  alignas(64) unsigned char m[kMaxBlocksPerLaunch][128];
+};
+
 // Host-side launchers (defined in the .cu files).
-cudaError_t launch_cmac(const void *tmap /* CUtensorMap, 64 B */, const XParams &p, int grid,
-                        int smem_bytes, cudaStream_t stream);
+cudaError_t launch_cmac(const XMaps &maps, const XParams &p, int grid, int smem_bytes,
+                        cudaStream_t stream);
 cudaError_t cmac_set_smem(int smem_bytes);
 cudaError_t launch_dump(int64_t *acc, int64_t *vis, int64_t *stokes, int n_ant, int n_pol,
                         int n_chan, cudaStream_t stream, int grid);

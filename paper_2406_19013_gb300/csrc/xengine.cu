@@ -9,20 +9,24 @@
 // [a, b] (used on both sides) and a "Q row" [b, -a] (row side only).  That is
 // a dense rank-2T update, so it runs on the tensor cores: fp16 operands (every
 // value in [-8, 8] is exact in fp16) and fp32 accumulators in TMEM.  Each
-// product is an integer of magnitude <= 64 and each block's partial sums stay
-// below 128 * block_len < 2^24, so every fp32 accumulation is exact; the
-// partials are folded into the int64 integration buffer once per block.
+// product is an integer of magnitude <= 64 and the partial sums of a launch
+// stay below 128 * (samples per launch) < 2^24, so every fp32 accumulation is
+// exact; the
+// partials are folded into the int64 integration buffer once per launch.
 //
-// Kernel structure (persistent, one CTA per SM, 10 warps):
-//   warp 8      TMA producer: packed bytes [channel][input][time] -> smem ring
-//   warps 0-3   unpack: 4-bit nibbles -> fp16 A/Q rows in the 128B-swizzled
+// Kernel structure (persistent, one CTA per SM, 17 warps):
+//   warp 12     TMA producer: packed bytes [channel][input][time] -> smem ring
+//   warps 0-7   unpack: 4-bit nibbles -> fp16 A/Q rows in the 128B-swizzled
 //               K-major layout the MMA reads (the paper's CPU "fluff" step,
 //               Sec. 2.3, moved on chip)
-//   warp 9      MMA issuer: tcgen05.mma M=128 (64 inputs' A rows + Q rows),
-//               N = columns of the triangle strip, K = 16 per instruction
-//   warps 4-7   epilogue: tcgen05.ld of the fp32 accumulators, exchange of
-//               re/im between lanes, int64 read-modify-write of the lower
-//               triangle in HBM
+//   warps 13-16 MMA issuers: tcgen05.mma M=128 (64 inputs' A rows + Q rows),
+//               N = columns of the triangle strip, K = 16 per instruction;
+//               one issuing thread per accumulator, because a single thread
+//               issues an MMA only every ~200 cycles whatever its size
+//   warps 8-11  epilogue: tcgen05.ld of the fp32 accumulators, exchange of
+//               re/im between lanes, int64 red.add into the lower triangle
+// A launch integrates up to kMaxBlocksPerLaunch blocks before the fold, as
+// long as the samples per fold keep every fp32 partial below 2^24.
 // A work unit is (channel, template); a template names the inputs staged
 // per chunk and the MMAs (row tile x column range) that cover its part of
 // the triangle.  All waits are bounded by a timeout; on expiry the kernel
@@ -70,10 +74,16 @@ struct Bars {
   uint32_t pk_full, pk_empty, z_full, z_empty, acc_full, acc_empty, drain;
 };
 
+// Fire-and-forget 64-bit add in L2 (no return value, no round trip).
+__device__ __forceinline__ void red_add_s64(int64_t *addr, long long v) {
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(addr), "l"((unsigned long long)v) : "memory");
+}
+
 }  // namespace
 
+// kThreads = 32 * 17: warps 0-7 unpack, 8-11 epilogue, 12 TMA, 13-16 MMA.
 __global__ void __launch_bounds__(kThreads, 1)
-    xengine_cmac_kernel(const __grid_constant__ CUtensorMap tmap, const XParams p) {
+    xengine_cmac_kernel(const __grid_constant__ XMaps maps, const XParams p) {
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte alignment for the swizzled operand atoms
   uint8_t *smem = reinterpret_cast<uint8_t *>(
@@ -81,8 +91,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t *z_buf = smem;
   uint8_t *pk_buf = z_buf + (size_t)p.z_stages * p.z_stage_bytes;
   uint64_t *bar_mem = reinterpret_cast<uint64_t *>(pk_buf + (size_t)p.pk_stages * p.pk_stage_bytes);
-  // [pk_full x S][pk_empty x S][z_full x Z][z_empty x Z][acc_full][acc_empty][drain]
-  uint32_t *misc = reinterpret_cast<uint32_t *>(bar_mem + 2 * p.pk_stages + 2 * p.z_stages + 3);
+  // [pk_full x S][pk_empty x S][z_full x Z][z_empty x Z][acc_full][acc_empty][drain x kMmaWarps]
+  uint32_t *misc = reinterpret_cast<uint32_t *>(bar_mem + 2 * p.pk_stages + 2 * p.z_stages + 2 +
+                                                kMmaWarps);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(misc + 1);
   const uint32_t bar0 = smem_u32(bar_mem);
   Bars b;
@@ -99,19 +110,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.pk_stages; ++s) {
       mbar_init(b.pk_full + 8 * s, 1);
-      mbar_init(b.pk_empty + 8 * s, 4);
+      mbar_init(b.pk_empty + 8 * s, kUnpackWarps);
     }
     for (int s = 0; s < p.z_stages; ++s) {
-      mbar_init(b.z_full + 8 * s, 4);
-      mbar_init(b.z_empty + 8 * s, 1);
+      mbar_init(b.z_full + 8 * s, kUnpackWarps);
+      mbar_init(b.z_empty + 8 * s, kMmaWarps);
     }
-    mbar_init(b.acc_full, 1);
-    mbar_init(b.acc_empty, 4);
-    mbar_init(b.drain, 1);
+    mbar_init(b.acc_full, kMmaWarps);
+    mbar_init(b.acc_empty, kEpiWarps);
+    for (int m = 0; m < kMmaWarps; ++m) mbar_init(b.drain + 8 * m, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 9) {
+  if (warp == kWarpMma0) {
     tmem_alloc(smem_u32(misc), kTmemCols);
     tmem_relinquish();
   }
@@ -121,12 +132,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = misc[0];
 
   const long long n_work = (long long)p.n_tpl * p.n_chan;
+  const int n_chunks = p.chunks_per_block * p.n_blocks;
   const uint64_t to = p.timeout_ns;
 
-  if (warp == 8) {
+  if (warp == kWarpTma) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      prefetch_tmap(&tmap);
+      for (int k = 0; k < p.n_blocks; ++k) prefetch_tmap(&maps.m[k][0]);
       int s = 0;
       uint32_t ph = 0;
       int armed[8];
@@ -138,7 +150,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const XUnit *u = p.units + tpl;
         const int n_reg = u->n_reg;
         const uint32_t bytes = (uint32_t)u->pk_bytes;
-        for (int k = 0; k < p.n_chunks; ++k) {
+        for (int k = 0; k < n_chunks; ++k) {
+          const int blk = k / p.chunks_per_block, kc = k - blk * p.chunks_per_block;
+          const void *tmap = &maps.m[blk][0];
           if (!mbar_wait(b.pk_empty + 8 * s, ph ^ 1u, abort_flag, to)) { ok = false; break; }
           const uint32_t full = b.pk_full + 8 * s;
           mbar_arrive_expect_tx(full, bytes);
@@ -148,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int r = 0; r < n_reg; ++r) {
             const int in_lo = u->reg[r].in_lo, n_in = u->reg[r].n_in, off = u->reg[r].pk_off;
             for (int bx = 0; bx < n_in; bx += kTileInputs)
-              tma_load_3d(dst0 + off + bx * kPackedRowBytes, &tmap, full, k * kChunkSamples,
+              tma_load_3d(dst0 + off + bx * kPackedRowBytes, tmap, full, kc * kChunkSamples,
                           in_lo + bx, c);
           }
           if (++s == p.pk_stages) { s = 0; ph ^= 1u; }
@@ -159,8 +173,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int k = 0; k < p.pk_stages; ++k)
         if (armed[k]) mbar_wait(b.pk_full + 8 * k, armed_ph[k], &dummy, to);
     }
-  } else if (warp == 9) {
-    // ------------------------------------------------------------ MMA issuer
+  } else if (warp >= kWarpMma0) {
+    // ------------------------------------------------------------ MMA issuers
+    // Issuer m owns the accumulators of segments m, m + kMmaWarps, ...; one
+    // thread per warp, so independent accumulators are fed by parallel
+    // instruction streams.
+    const int m = warp - kWarpMma0;
     if (lane == 0) {
       int zs = 0;
       uint32_t zph = 0;
@@ -169,14 +187,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (long long w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++nu) {
         const XUnit *u = p.units + (int)(w / p.n_chan);
         const int n_seg = u->n_seg;
+        XSeg mine[kMaxSegs / kMmaWarps];
+        int n_mine = 0;
+        for (int sg = m; sg < n_seg; sg += kMmaWarps) mine[n_mine++] = u->seg[sg];
         if (nu > 0 && !mbar_wait(b.acc_empty, (uint32_t)((nu - 1) & 1), abort_flag, to)) break;
         tc_fence_after();
-        for (int k = 0; k < p.n_chunks; ++k) {
+        for (int k = 0; k < n_chunks; ++k) {
           if (!mbar_wait(b.z_full + 8 * zs, zph, abort_flag, to)) { ok = false; break; }
           tc_fence_after();
           const uint32_t zb = smem_u32(z_buf + (size_t)zs * p.z_stage_bytes);
-          for (int sg = 0; sg < n_seg; ++sg) {
-            const XSeg sgm = u->seg[sg];
+          for (int j = 0; j < n_mine; ++j) {
+            const XSeg &sgm = mine[j];
             const uint32_t idesc = idesc_f16_f32(128, sgm.n);
             const uint32_t a0 = zb + (uint32_t)sgm.a_zrow * 128u;
             const uint32_t b0 = zb + (uint32_t)sgm.b_zrow * 128u;
@@ -193,45 +214,49 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (ok) mma_commit(b.acc_full);
       }
       // all MMAs this thread issued complete before TMEM is released
-      mma_commit(b.drain);
+      mma_commit(b.drain + 8 * m);
       int dummy = 0;
-      mbar_wait(b.drain, 0, &dummy, to);
+      mbar_wait(b.drain + 8 * m, 0, &dummy, to);
     }
-  } else if (warp < 4) {
+  } else if (warp < kUnpackWarps) {
     // ------------------------------------------------------------ unpack
-    const int tid = threadIdx.x;  // 0..127
+    // Work item = (input row, 8-sample quarter of the 32-sample chunk).
+    const int tid = threadIdx.x;
+    constexpr int kUnpackThreads = 32 * kUnpackWarps;
     int s = 0, zs = 0;
     uint32_t ph = 0, zph = 0;
     bool ok = true;
     for (long long w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
       const XUnit *u = p.units + (int)(w / p.n_chan);
       const int n_reg = u->n_reg;
-      for (int k = 0; k < p.n_chunks; ++k) {
+      XRegion rgs[2];
+      for (int r = 0; r < n_reg; ++r) rgs[r] = u->reg[r];
+      for (int k = 0; k < n_chunks; ++k) {
         if (!mbar_wait(b.pk_full + 8 * s, ph, abort_flag, to)) { ok = false; break; }
         if (!mbar_wait(b.z_empty + 8 * zs, zph ^ 1u, abort_flag, to)) { ok = false; break; }
         const uint8_t *pk = pk_buf + (size_t)s * p.pk_stage_bytes;
         uint8_t *zst = z_buf + (size_t)zs * p.z_stage_bytes;
         for (int r = 0; r < n_reg; ++r) {
-          const XRegion rg = u->reg[r];
+          const XRegion rg = rgs[r];
           const uint8_t *pkr = pk + rg.pk_off;
           uint8_t *zr = zst + (size_t)rg.z_row * 128;
-          const int items = rg.n_in * 2;
-          for (int it = tid; it < items; it += 128) {
-            const int row = it >> 1, h = it & 1;
-            const uint4 in = *reinterpret_cast<const uint4 *>(pkr + row * 32 + h * 16);
+          const int items = rg.n_in * 4;
+          for (int it = tid; it < items; it += kUnpackThreads) {
+            const int row = it >> 2, qt = it & 3;
+            const uint2 in = *reinterpret_cast<const uint2 *>(pkr + row * 32 + qt * 8);
             const int rho = rg.interleaved ? (((row >> 3) << 4) | (row & 7)) : row;
             uint8_t *pa = zr + (size_t)rho * 128;
             uint8_t *pq = pa + 8 * 128;
             const int sw = row & 7;
-            const uint32_t wv[4] = {in.x, in.y, in.z, in.w};
-#pragma unroll
-            for (int wi = 0; wi < 4; ++wi) {
-              uint4 va, vq;
-              decode_word(wv[wi], va, vq);
-              const int off = ((4 * h + wi) ^ sw) << 4;
-              *reinterpret_cast<uint4 *>(pa + off) = va;
-              if (rg.interleaved) *reinterpret_cast<uint4 *>(pq + off) = vq;
-            }
+            uint4 va, vq;
+            decode_word(in.x, va, vq);
+            const int off0 = ((2 * qt) ^ sw) << 4;
+            *reinterpret_cast<uint4 *>(pa + off0) = va;
+            if (rg.interleaved) *reinterpret_cast<uint4 *>(pq + off0) = vq;
+            decode_word(in.y, va, vq);
+            const int off1 = ((2 * qt + 1) ^ sw) << 4;
+            *reinterpret_cast<uint4 *>(pa + off1) = va;
+            if (rg.interleaved) *reinterpret_cast<uint4 *>(pq + off1) = vq;
           }
         }
         fence_proxy_async_smem();
@@ -244,9 +269,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (++zs == p.z_stages) { zs = 0; zph ^= 1u; }
       }
     }
-  } else {
+  } else if (warp < kWarpTma) {
     // ------------------------------------------------------------ epilogue
-    const int q = warp & 3;
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int rho = 32 * q + lane;
     const int g = rho >> 4, is_im = (rho >> 3) & 1, l = rho & 7;
     long long nu = 0;
@@ -278,20 +303,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           const int j0 = sgm.col_in0 + cb + (is_im ? 8 : 0);
           const int nvalid = row_ok ? min(8, i - j0 + 1) : 0;
-          if (nvalid > 0) {
-            longlong2 *ptr = reinterpret_cast<longlong2 *>(arow + 2 * (long long)j0);
-            longlong2 old[8];
+          int64_t *ptr = arow + 2 * (long long)j0;
 #pragma unroll
-            for (int e = 0; e < 8; ++e)
-              if (e < nvalid) old[e] = ptr[e];
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-              if (e < nvalid) {
-                old[e].x += re[e];
-                old[e].y += im[e];
-                ptr[e] = old[e];
-              }
-          }
+          for (int e = 0; e < 8; ++e)
+            if (e < nvalid) {
+              red_add_s64(ptr + 2 * e, re[e]);
+              red_add_s64(ptr + 2 * e + 1, im[e]);
+            }
         }
       }
       tc_fence_before();
@@ -302,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   tc_fence_before();
   __syncthreads();
-  if (warp == 9) {
+  if (warp == kWarpMma0) {
     __syncwarp();
     tc_fence_after();
     tmem_dealloc(tmem, kTmemCols);
@@ -315,10 +333,9 @@ cudaError_t cmac_set_smem(int smem_bytes) {
                               smem_bytes);
 }
 
-cudaError_t launch_cmac(const void *tmap, const XParams &p, int grid, int smem_bytes,
+cudaError_t launch_cmac(const XMaps &maps, const XParams &p, int grid, int smem_bytes,
                         cudaStream_t stream) {
-  CUtensorMap m = *reinterpret_cast<const CUtensorMap *>(tmap);
-  xengine_cmac_kernel<<<grid, kThreads, smem_bytes, stream>>>(m, p);
+  xengine_cmac_kernel<<<grid, kThreads, smem_bytes, stream>>>(maps, p);
   return cudaGetLastError();
 }
 

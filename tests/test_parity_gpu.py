@@ -80,6 +80,50 @@ def test_ragged_shapes(corr, torch_cuda, oracle_mod, synth_mod, n_ant, n_pol, C,
         assert np.array_equal(st, ost)
 
 
+@pytest.mark.parametrize("n_ant,n_pol,C,T,nb", [
+    (20, 2, 3, 20000, 7),    # 6 blocks per launch (6 * 20000 <= 131071), then 1
+    (96, 2, 4, 8192, 9),     # 8 blocks per launch, then 1
+    (9, 1, 5, 1000, 3),      # pitched staging: one block per launch
+])
+def test_push_blocks_groups(corr, torch_cuda, oracle_mod, synth_mod, n_ant, n_pol, C, T, nb):
+    torch = torch_cuda
+    N = n_ant * n_pol
+    blocks = [synth_mod.make_block(N, C, T, seed=7, block=b) for b in range(nb)]
+    dev = [torch.from_numpy(b).cuda() for b in blocks]
+    with corr.Correlator(n_ant, n_pol, C, T) as xc:
+        n0 = xc.launch_count()
+        xc.push_blocks(dev)
+        assert xc.samples_integrated() == nb * T
+        vis, st = xc.dump()
+        xc.check()
+        launches = xc.launch_count() - n0
+    ov, ost = _oracle(oracle_mod, blocks, n_ant, n_pol)
+    assert np.array_equal(vis.cpu().numpy(), ov)
+    if n_pol == 2:
+        assert np.array_equal(st.cpu().numpy(), ost)
+    per = 1 if T % 16 else min(8, 131071 // T)
+    cmac_launches = -(-nb // per)
+    assert launches == cmac_launches + (nb if T % 16 else 0) + 1
+
+
+def test_push_blocks_rejects(corr, torch_cuda):
+    torch = torch_cuda
+    with corr.Correlator(4, 2, 2, 64) as xc:
+        with pytest.raises(corr.CorrError) as e:
+            xc.push_blocks([])
+        assert e.value.code == corr.CORR_EINVAL
+        good = torch.zeros(2 * 8 * 64 + 16, dtype=torch.uint8, device="cuda")
+        with pytest.raises(corr.CorrError) as e:
+            xc.push_blocks([good.data_ptr(), good.data_ptr() + 8])  # misaligned second block
+        assert e.value.code == corr.CORR_EINVAL
+        with pytest.raises(corr.CorrError):
+            xc.push_blocks([good.data_ptr(), 0])
+        # nothing was enqueued by the rejected calls
+        assert xc.samples_integrated() == 0
+        v, _ = xc.dump()
+        assert not v.cpu().numpy().any()
+
+
 def test_extremes_at_max_block_len(corr, torch_cuda, oracle_mod, synth_mod):
     # The largest block keeps every fp32 partial an exact integer: -8-8j on
     # every sample gives autos of 128 * 131071 = 16777088 (< 2^24).  The
