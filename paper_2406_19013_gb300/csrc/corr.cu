@@ -158,10 +158,10 @@ int encode_block_map(const corr_ctx *ctx, const void *base, CUtensorMap *m) {
                               (cuuint64_t)ctx->n_chan};
   const cuuint64_t strides[2] = {(cuuint64_t)ctx->pitch,
                                  (cuuint64_t)ctx->pitch * (cuuint64_t)ctx->n_in};
-  const cuuint32_t box[3] = {(cuuint32_t)xe::kChunkSamples, (cuuint32_t)xe::kTileInputs, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)xe::kPkSamples, (cuuint32_t)xe::kTileInputs, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(base), dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? CORR_OK : CORR_ECUDA;
 }
@@ -250,11 +250,16 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
     max_pk = std::max(max_pk, u.pk_bytes);
   }
   ctx->z_stage_bytes = (uint32_t)round_up(max_z * 128, 1024);
-  ctx->pk_stage_bytes = (uint32_t)round_up(max_pk, 128);
-  ctx->pk_stages = 4;
+  ctx->pk_stage_bytes = (uint32_t)round_up(max_pk, 1024);  // swizzled TMA destination
   const int fixed = 1024 /* alignment slack */ + 256 /* barriers, TMEM address, flags */;
   static_assert(8 * (2 * 4 + 2 * 4 + 2 + xe::kMmaWarps) + 8 <= 256, "barrier area");
-  int zs = (smem_optin - fixed - ctx->pk_stages * (int)ctx->pk_stage_bytes) / (int)ctx->z_stage_bytes;
+  // three packed stages (bytes in flight for HBM) if that leaves two or more
+  // operand stages, else two
+  int zs = 0;
+  for (int ps = 3; ps >= 2 && zs < 2; --ps) {
+    ctx->pk_stages = ps;
+    zs = (smem_optin - fixed - ps * (int)ctx->pk_stage_bytes) / (int)ctx->z_stage_bytes;
+  }
   zs = std::min(zs, 4);
   if (zs < 2) {
     free_ctx(ctx);
@@ -315,6 +320,7 @@ int corr_push_blocks(corr_ctx *ctx, const uint8_t *const *d_blocks, int n_blocks
   p.n_chan = ctx->n_chan;
   p.n_in = ctx->n_in;
   p.chunks_per_block = (ctx->block_len + xe::kChunkSamples - 1) / xe::kChunkSamples;
+  p.pk_per_block = (ctx->block_len + xe::kPkSamples - 1) / xe::kPkSamples;
   p.n_pairs = ctx->n_pairs;
   p.acc = ctx->d_acc;
   p.status = ctx->d_status;

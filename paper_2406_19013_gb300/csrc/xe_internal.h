@@ -15,7 +15,12 @@ constexpr int kTileInputs = 64;
 constexpr int kTmemCols = 512;
 constexpr int kMaxSegs = 8;
 constexpr int kMaxZRows = 512;
-constexpr int kPackedRowBytes = kChunkSamples;  // one byte per complex sample
+// Samples per TMA box row (one byte per complex sample): a packed stage holds
+// kPkSamples samples of every staged input and feeds kPkSamples /
+// kChunkSamples operand chunks.
+constexpr int kPkSamples = 128;
+constexpr int kPackedRowBytes = kPkSamples;
+constexpr int kChunksPerPk = kPkSamples / kChunkSamples;
 // Warp roles (see xengine.cu): unpack, epilogue (one per TMEM lane quarter),
 // TMA producer, MMA issuers (one issue stream per accumulator).
 constexpr int kUnpackWarps = 8;
@@ -66,6 +71,7 @@ struct XParams {
   int n_chan;
   int n_in;
   int chunks_per_block;  // ceil(block_len / kChunkSamples)
+  int pk_per_block;      // ceil(block_len / kPkSamples)
   int n_blocks;          // blocks in this launch (<= kMaxBlocksPerLaunch)
   long long n_pairs;   // N(N+1)/2
   int64_t *acc;        // [n_chan][n_pairs][2]

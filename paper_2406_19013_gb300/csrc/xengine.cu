@@ -40,34 +40,37 @@ namespace xe {
 
 namespace {
 
-// sub.f16x2 on raw bit patterns (exact here: small integers only).
-__device__ __forceinline__ uint32_t hsub2_bits(uint32_t a, uint32_t b) {
+__device__ __forceinline__ uint32_t hfma2_bits(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t d;
-  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
   return d;
 }
 
-// Four packed samples (bytes of w, earliest in the low byte) -> the 16-byte
-// A-row chunk [a0 b0 a1 b1 a2 b2 a3 b3] and Q-row chunk [b0 -a0 b1 -a1 ...]
-// in fp16.  A nibble n encodes n - 16*(n >= 8); (n ^ 8) = value + 8, and
-// fp16 0x6400 | k is 1024 + k, so subtracting 1032 leaves the value.
+// Four packed samples t0..t3 (bytes of w, earliest in the low byte) -> the
+// 16-byte A-row chunk and Q-row chunk of those samples in fp16.  The K order
+// inside a chunk is [a0 a2 b0 b2 a1 a3 b1 b3] for the A row and
+// [b0 b2 -a0 -a2 b1 b3 -a1 -a3] for the Q row: any fixed order of K gives
+// the same dot products as long as every row uses it, and this one needs no
+// byte shuffles.  A nibble n encodes n - 16 (n >= 8); with u = n ^ 8 the
+// value is u - 8.  fp16 0x6400 | k is 1024 + k, so
+//   low nibble  in bits 0-3 :  (0x6400 | u)      - 1032        = u - 8
+//   high nibble in bits 4-7 :  (0x6400 | 16 u) / 16 - 72       = u - 8
+// and the XOR with 8 folds into the constant of the same logic op.  All
+// values are small integers, so every fp16 step is exact.
 __device__ __forceinline__ void decode_word(uint32_t w, uint4 &a, uint4 &q) {
-  const uint32_t x = w ^ 0x88888888u;
-  const uint32_t lo = x & 0x0F0F0F0Fu;         // imaginary + 8, per byte
-  const uint32_t hi = (x >> 4) & 0x0F0F0F0Fu;  // real + 8, per byte
-  const uint32_t bias = 0x64086408u;           // fp16 (1032, 1032)
-  uint32_t r0 = (__byte_perm(hi, lo, 0x4400) & 0x00FF00FFu) | 0x64006400u;
-  uint32_t r1 = (__byte_perm(hi, lo, 0x5511) & 0x00FF00FFu) | 0x64006400u;
-  uint32_t r2 = (__byte_perm(hi, lo, 0x6622) & 0x00FF00FFu) | 0x64006400u;
-  uint32_t r3 = (__byte_perm(hi, lo, 0x7733) & 0x00FF00FFu) | 0x64006400u;
-  r0 = hsub2_bits(r0, bias);
-  r1 = hsub2_bits(r1, bias);
-  r2 = hsub2_bits(r2, bias);
-  r3 = hsub2_bits(r3, bias);
-  a = make_uint4(r0, r1, r2, r3);
-  // swap halves -> (b, a), flip the sign of the upper half -> (b, -a)
-  q = make_uint4(__byte_perm(r0, 0, 0x1032) ^ 0x80000000u, __byte_perm(r1, 0, 0x1032) ^ 0x80000000u,
-                 __byte_perm(r2, 0, 0x1032) ^ 0x80000000u, __byte_perm(r3, 0, 0x1032) ^ 0x80000000u);
+  const uint32_t s16 = 0x2C002C00u, m72 = 0xD480D480u;    // (1/16, 1/16), (-72, -72)
+  const uint32_t ns16 = 0xAC00AC00u, p72 = 0x54805480u;   // (-1/16, -1/16), (72, 72)
+  const uint32_t one = 0x3C003C00u, m1032 = 0xE408E408u;  // (1, 1), (-1032, -1032)
+  const uint32_t w8 = w >> 8;
+  const uint32_t lo02 = (w & 0x000F000Fu) ^ 0x64086408u;   // samples 0, 2: 1024 + u_im
+  const uint32_t hi02 = (w & 0x00F000F0u) ^ 0x64806480u;   //               1024 + 16 u_re
+  const uint32_t lo13 = (w8 & 0x000F000Fu) ^ 0x64086408u;  // samples 1, 3
+  const uint32_t hi13 = (w8 & 0x00F000F0u) ^ 0x64806480u;
+  const uint32_t re02 = hfma2_bits(hi02, s16, m72), im02 = hfma2_bits(lo02, one, m1032);
+  const uint32_t re13 = hfma2_bits(hi13, s16, m72), im13 = hfma2_bits(lo13, one, m1032);
+  const uint32_t nre02 = hfma2_bits(hi02, ns16, p72), nre13 = hfma2_bits(hi13, ns16, p72);
+  a = make_uint4(re02, im02, re13, im13);
+  q = make_uint4(im02, nre02, im13, nre13);
 }
 
 struct Bars {
@@ -150,8 +153,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const XUnit *u = p.units + tpl;
         const int n_reg = u->n_reg;
         const uint32_t bytes = (uint32_t)u->pk_bytes;
-        for (int k = 0; k < n_chunks; ++k) {
-          const int blk = k / p.chunks_per_block, kc = k - blk * p.chunks_per_block;
+        const int n_pk = p.pk_per_block * p.n_blocks;
+        for (int k = 0; k < n_pk; ++k) {
+          const int blk = k / p.pk_per_block, kc = k - blk * p.pk_per_block;
           const void *tmap = &maps.m[blk][0];
           if (!mbar_wait(b.pk_empty + 8 * s, ph ^ 1u, abort_flag, to)) { ok = false; break; }
           const uint32_t full = b.pk_full + 8 * s;
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int r = 0; r < n_reg; ++r) {
             const int in_lo = u->reg[r].in_lo, n_in = u->reg[r].n_in, off = u->reg[r].pk_off;
             for (int bx = 0; bx < n_in; bx += kTileInputs)
-              tma_load_3d(dst0 + off + bx * kPackedRowBytes, tmap, full, kc * kChunkSamples,
+              tma_load_3d(dst0 + off + bx * kPackedRowBytes, tmap, full, kc * kPkSamples,
                           in_lo + bx, c);
           }
           if (++s == p.pk_stages) { s = 0; ph ^= 1u; }
@@ -231,42 +235,49 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int n_reg = u->n_reg;
       XRegion rgs[2];
       for (int r = 0; r < n_reg; ++r) rgs[r] = u->reg[r];
-      for (int k = 0; k < n_chunks; ++k) {
-        if (!mbar_wait(b.pk_full + 8 * s, ph, abort_flag, to)) { ok = false; break; }
-        if (!mbar_wait(b.z_empty + 8 * zs, zph ^ 1u, abort_flag, to)) { ok = false; break; }
-        const uint8_t *pk = pk_buf + (size_t)s * p.pk_stage_bytes;
-        uint8_t *zst = z_buf + (size_t)zs * p.z_stage_bytes;
-        for (int r = 0; r < n_reg; ++r) {
-          const XRegion rg = rgs[r];
-          const uint8_t *pkr = pk + rg.pk_off;
-          uint8_t *zr = zst + (size_t)rg.z_row * 128;
-          const int items = rg.n_in * 4;
-          for (int it = tid; it < items; it += kUnpackThreads) {
-            const int row = it >> 2, qt = it & 3;
-            const uint2 in = *reinterpret_cast<const uint2 *>(pkr + row * 32 + qt * 8);
-            const int rho = rg.interleaved ? (((row >> 3) << 4) | (row & 7)) : row;
-            uint8_t *pa = zr + (size_t)rho * 128;
-            uint8_t *pq = pa + 8 * 128;
-            const int sw = row & 7;
-            uint4 va, vq;
-            decode_word(in.x, va, vq);
-            const int off0 = ((2 * qt) ^ sw) << 4;
-            *reinterpret_cast<uint4 *>(pa + off0) = va;
-            if (rg.interleaved) *reinterpret_cast<uint4 *>(pq + off0) = vq;
-            decode_word(in.y, va, vq);
-            const int off1 = ((2 * qt + 1) ^ sw) << 4;
-            *reinterpret_cast<uint4 *>(pa + off1) = va;
-            if (rg.interleaved) *reinterpret_cast<uint4 *>(pq + off1) = vq;
+      for (int blk = 0; blk < p.n_blocks && ok; ++blk) {
+        for (int kb = 0; kb < p.chunks_per_block; ++kb) {
+          const int sub = kb % kChunksPerPk;  // operand chunk within the packed stage
+          if (sub == 0 && !mbar_wait(b.pk_full + 8 * s, ph, abort_flag, to)) { ok = false; break; }
+          if (!mbar_wait(b.z_empty + 8 * zs, zph ^ 1u, abort_flag, to)) { ok = false; break; }
+          const uint8_t *pk = pk_buf + (size_t)s * p.pk_stage_bytes;
+          uint8_t *zst = z_buf + (size_t)zs * p.z_stage_bytes;
+          for (int r = 0; r < n_reg; ++r) {
+            const XRegion rg = rgs[r];
+            const uint8_t *pkr = pk + rg.pk_off;
+            uint8_t *zr = zst + (size_t)rg.z_row * 128;
+            const int items = rg.n_in * 4;
+            for (int it = tid; it < items; it += kUnpackThreads) {
+              const int row = it >> 2, qt = it & 3;
+              // packed rows arrive 128B-swizzled: 16-byte chunk c of row r sits at c ^ (r & 7)
+              const int c16 = (2 * sub + (qt >> 1)) ^ (row & 7);
+              const uint2 in = *reinterpret_cast<const uint2 *>(pkr + row * kPackedRowBytes +
+                                                                c16 * 16 + (qt & 1) * 8);
+              const int rho = rg.interleaved ? (((row >> 3) << 4) | (row & 7)) : row;
+              uint8_t *pa = zr + (size_t)rho * 128;
+              uint8_t *pq = pa + 8 * 128;
+              const int sw = row & 7;
+              uint4 va, vq;
+              decode_word(in.x, va, vq);
+              const int off0 = ((2 * qt) ^ sw) << 4;
+              *reinterpret_cast<uint4 *>(pa + off0) = va;
+              if (rg.interleaved) *reinterpret_cast<uint4 *>(pq + off0) = vq;
+              decode_word(in.y, va, vq);
+              const int off1 = ((2 * qt + 1) ^ sw) << 4;
+              *reinterpret_cast<uint4 *>(pa + off1) = va;
+              if (rg.interleaved) *reinterpret_cast<uint4 *>(pq + off1) = vq;
+            }
           }
+          fence_proxy_async_smem();
+          __syncwarp();
+          const bool last_of_pk = sub == kChunksPerPk - 1 || kb == p.chunks_per_block - 1;
+          if (lane == 0) {
+            mbar_arrive(b.z_full + 8 * zs);
+            if (last_of_pk) mbar_arrive(b.pk_empty + 8 * s);
+          }
+          if (last_of_pk && ++s == p.pk_stages) { s = 0; ph ^= 1u; }
+          if (++zs == p.z_stages) { zs = 0; zph ^= 1u; }
         }
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(b.z_full + 8 * zs);
-          mbar_arrive(b.pk_empty + 8 * s);
-        }
-        if (++s == p.pk_stages) { s = 0; ph ^= 1u; }
-        if (++zs == p.z_stages) { zs = 0; zph ^= 1u; }
       }
     }
   } else if (warp < kWarpTma) {
