@@ -6,9 +6,9 @@
 
 namespace xe {
 
-// Samples per pipeline chunk: one 128-byte row of fp16 (re, im) pairs, i.e.
-// exactly one 128B-swizzle atom along K.
-constexpr int kChunkSamples = 32;
+// Samples per pipeline chunk: one 128-byte operand row of fp8 (e5m2) values,
+// two per sample (re, im), i.e. exactly one 128B-swizzle atom along K.
+constexpr int kChunkSamples = 64;
 // Inputs per row tile: the MMA A operand stacks 64 inputs' real-part rows and
 // 64 inputs' imaginary-part rows (M = 128).
 constexpr int kTileInputs = 64;
@@ -23,7 +23,7 @@ constexpr int kPackedRowBytes = kPkSamples;
 constexpr int kChunksPerPk = kPkSamples / kChunkSamples;
 // Warp roles (see xengine.cu): unpack, epilogue (one per TMEM lane quarter),
 // TMA producer, MMA issuers (one issue stream per accumulator).
-constexpr int kUnpackWarps = 8;
+constexpr int kUnpackWarps = 16;
 constexpr int kEpiWarps = 4;
 constexpr int kMmaWarps = 4;
 constexpr int kWarpEpi0 = kUnpackWarps;

@@ -7,23 +7,23 @@
 // so with K running over (t, re/im) the whole channel is one real matrix
 // product D = Arows * Brows^T, where every input contributes an "A row"
 // [a, b] (used on both sides) and a "Q row" [b, -a] (row side only).  That is
-// a dense rank-2T update, so it runs on the tensor cores: fp16 operands (every
-// value in [-8, 8] is exact in fp16) and fp32 accumulators in TMEM.  Each
-// product is an integer of magnitude <= 64 and the partial sums of a launch
-// stay below 128 * (samples per launch) < 2^24, so every fp32 accumulation is
-// exact; the
+// a dense rank-2T update, so it runs on the tensor cores: 8-bit float operands
+// (E5M2: every integer in [-8, 8] is exact) and fp32 accumulators in TMEM.
+// Each product is an integer of magnitude <= 64 and the partial sums of a
+// launch stay below 128 * (samples per launch) < 2^24, so every fp32
+// accumulation is exact; the
 // partials are folded into the int64 integration buffer once per launch.
 //
-// Kernel structure (persistent, one CTA per SM, 17 warps):
-//   warp 12     TMA producer: packed bytes [channel][input][time] -> smem ring
-//   warps 0-7   unpack: 4-bit nibbles -> fp16 A/Q rows in the 128B-swizzled
+// Kernel structure (persistent, one CTA per SM, 25 warps):
+//   warp 20     TMA producer: packed bytes [channel][input][time] -> smem ring
+//   warps 0-15  unpack: 4-bit nibbles -> E5M2 A/Q rows in the 128B-swizzled
 //               K-major layout the MMA reads (the paper's CPU "fluff" step,
 //               Sec. 2.3, moved on chip)
-//   warps 13-16 MMA issuers: tcgen05.mma M=128 (64 inputs' A rows + Q rows),
-//               N = columns of the triangle strip, K = 16 per instruction;
+//   warps 21-24 MMA issuers: tcgen05.mma M=128 (64 inputs' A rows + Q rows),
+//               N = columns of the triangle strip, K = 32 per instruction;
 //               one issuing thread per accumulator, because a single thread
 //               issues an MMA only every ~200 cycles whatever its size
-//   warps 8-11  epilogue: tcgen05.ld of the fp32 accumulators, exchange of
+//   warps 16-19 epilogue: tcgen05.ld of the fp32 accumulators, exchange of
 //               re/im between lanes, int64 red.add into the lower triangle
 // A launch integrates up to kMaxBlocksPerLaunch blocks before the fold, as
 // long as the samples per fold keep every fp32 partial below 2^24.
@@ -47,17 +47,20 @@ __device__ __forceinline__ uint32_t hfma2_bits(uint32_t a, uint32_t b, uint32_t 
 }
 
 // Four packed samples t0..t3 (bytes of w, earliest in the low byte) -> the
-// 16-byte A-row chunk and Q-row chunk of those samples in fp16.  The K order
-// inside a chunk is [a0 a2 b0 b2 a1 a3 b1 b3] for the A row and
-// [b0 b2 -a0 -a2 b1 b3 -a1 -a3] for the Q row: any fixed order of K gives
-// the same dot products as long as every row uses it, and this one needs no
-// byte shuffles.  A nibble n encodes n - 16 (n >= 8); with u = n ^ 8 the
-// value is u - 8.  fp16 0x6400 | k is 1024 + k, so
+// 8-byte A-row and Q-row pieces of those samples in E5M2.  The K order inside
+// a piece is [a0 a2 b0 b2 a1 a3 b1 b3] for the A row and
+// [b0 b2 -a0 -a2 b1 b3 -a1 -a3] for the Q row: any fixed order of K gives the
+// same dot products as long as every row uses it, and this one needs no
+// per-sample shuffles.  A nibble n encodes n - 16 (n >= 8); with u = n ^ 8
+// the value is u - 8.  fp16 0x6400 | k is 1024 + k, so
 //   low nibble  in bits 0-3 :  (0x6400 | u)      - 1032        = u - 8
 //   high nibble in bits 4-7 :  (0x6400 | 16 u) / 16 - 72       = u - 8
-// and the XOR with 8 folds into the constant of the same logic op.  All
-// values are small integers, so every fp16 step is exact.
-__device__ __forceinline__ void decode_word(uint32_t w, uint4 &a, uint4 &q) {
+// (the XOR with 8 folds into the constant of the same logic op; every fp16
+// step is exact on these small integers).  An integer of magnitude <= 8 has
+// at most 3 significant bits, so its fp16 encoding has a zero low byte and
+// its high byte is exactly its E5M2 encoding: one byte permute per four
+// values converts.
+__device__ __forceinline__ void decode_word(uint32_t w, uint2 &a, uint2 &q) {
   const uint32_t s16 = 0x2C002C00u, m72 = 0xD480D480u;    // (1/16, 1/16), (-72, -72)
   const uint32_t ns16 = 0xAC00AC00u, p72 = 0x54805480u;   // (-1/16, -1/16), (72, 72)
   const uint32_t one = 0x3C003C00u, m1032 = 0xE408E408u;  // (1, 1), (-1032, -1032)
@@ -69,8 +72,9 @@ __device__ __forceinline__ void decode_word(uint32_t w, uint4 &a, uint4 &q) {
   const uint32_t re02 = hfma2_bits(hi02, s16, m72), im02 = hfma2_bits(lo02, one, m1032);
   const uint32_t re13 = hfma2_bits(hi13, s16, m72), im13 = hfma2_bits(lo13, one, m1032);
   const uint32_t nre02 = hfma2_bits(hi02, ns16, p72), nre13 = hfma2_bits(hi13, ns16, p72);
-  a = make_uint4(re02, im02, re13, im13);
-  q = make_uint4(im02, nre02, im13, nre13);
+  // high bytes of (x.lo, x.hi, y.lo, y.hi)
+  a = make_uint2(__byte_perm(re02, im02, 0x7531), __byte_perm(re13, im13, 0x7531));
+  q = make_uint2(__byte_perm(im02, nre02, 0x7531), __byte_perm(im13, nre13, 0x7531));
 }
 
 struct Bars {
@@ -84,7 +88,7 @@ __device__ __forceinline__ void red_add_s64(int64_t *addr, long long v) {
 
 }  // namespace
 
-// kThreads = 32 * 17: warps 0-7 unpack, 8-11 epilogue, 12 TMA, 13-16 MMA.
+// kThreads = 32 * 25: warps 0-15 unpack, 16-19 epilogue, 20 TMA, 21-24 MMA.
 __global__ void __launch_bounds__(kThreads, 1)
     xengine_cmac_kernel(const __grid_constant__ XMaps maps, const XParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -202,14 +206,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t zb = smem_u32(z_buf + (size_t)zs * p.z_stage_bytes);
           for (int j = 0; j < n_mine; ++j) {
             const XSeg &sgm = mine[j];
-            const uint32_t idesc = idesc_f16_f32(128, sgm.n);
+            const uint32_t idesc = idesc_e5m2_f32(128, sgm.n);
             const uint32_t a0 = zb + (uint32_t)sgm.a_zrow * 128u;
             const uint32_t b0 = zb + (uint32_t)sgm.b_zrow * 128u;
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
               const uint64_t da = sdesc_sw128(a0 + 32u * kk, 1024u);
               const uint64_t db = sdesc_sw128(b0 + 32u * kk, (uint32_t)sgm.b_sbo);
-              mma_f16_ss(tmem + (uint32_t)sgm.tmem_col, da, db, idesc, (k | kk) != 0);
+              mma_f8_ss(tmem + (uint32_t)sgm.tmem_col, da, db, idesc, (k | kk) != 0);
             }
           }
           mma_commit(b.z_empty + 8 * zs);
@@ -246,26 +250,38 @@ __global__ void __launch_bounds__(kThreads, 1)
             const XRegion rg = rgs[r];
             const uint8_t *pkr = pk + rg.pk_off;
             uint8_t *zr = zst + (size_t)rg.z_row * 128;
-            const int items = rg.n_in * 4;
-            for (int it = tid; it < items; it += kUnpackThreads) {
-              const int row = it >> 2, qt = it & 3;
-              // packed rows arrive 128B-swizzled: 16-byte chunk c of row r sits at c ^ (r & 7)
-              const int c16 = (2 * sub + (qt >> 1)) ^ (row & 7);
-              const uint2 in = *reinterpret_cast<const uint2 *>(pkr + row * kPackedRowBytes +
-                                                                c16 * 16 + (qt & 1) * 8);
-              const int rho = rg.interleaved ? (((row >> 3) << 4) | (row & 7)) : row;
-              uint8_t *pa = zr + (size_t)rho * 128;
-              uint8_t *pq = pa + 8 * 128;
-              const int sw = row & 7;
-              uint4 va, vq;
-              decode_word(in.x, va, vq);
-              const int off0 = ((2 * qt) ^ sw) << 4;
-              *reinterpret_cast<uint4 *>(pa + off0) = va;
-              if (rg.interleaved) *reinterpret_cast<uint4 *>(pq + off0) = vq;
-              decode_word(in.y, va, vq);
-              const int off1 = ((2 * qt + 1) ^ sw) << 4;
-              *reinterpret_cast<uint4 *>(pa + off1) = va;
-              if (rg.interleaved) *reinterpret_cast<uint4 *>(pq + off1) = vq;
+            // work item = (input row, 8-sample group); 8 groups per 64-sample chunk
+            const int items = rg.n_in * 8;
+            // two work items per pass: their loads, decodes and stores interleave
+            for (int it0 = tid; it0 < items; it0 += 2 * kUnpackThreads) {
+              uint2 in[2];
+              int rowv[2], gv[2];
+              bool has[2];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int it = it0 + h * kUnpackThreads;
+                has[h] = it < items;
+                rowv[h] = has[h] ? (it >> 3) : 0;
+                gv[h] = it & 7;
+                // packed rows arrive 128B-swizzled: 16-byte chunk c of row r sits at c ^ (r & 7)
+                const int c16 = (4 * sub + (gv[h] >> 1)) ^ (rowv[h] & 7);
+                in[h] = *reinterpret_cast<const uint2 *>(pkr + rowv[h] * kPackedRowBytes + c16 * 16 +
+                                                         (gv[h] & 1) * 8);
+              }
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                if (!has[h]) continue;
+                const int row = rowv[h];
+                const int rho = rg.interleaved ? (((row >> 3) << 4) | (row & 7)) : row;
+                uint8_t *pa = zr + (size_t)rho * 128;
+                const int off = (gv[h] ^ (row & 7)) << 4;
+                uint2 a0, q0, a1, q1;
+                decode_word(in[h].x, a0, q0);
+                decode_word(in[h].y, a1, q1);
+                *reinterpret_cast<uint4 *>(pa + off) = make_uint4(a0.x, a0.y, a1.x, a1.y);
+                if (rg.interleaved)
+                  *reinterpret_cast<uint4 *>(pa + 8 * 128 + off) = make_uint4(q0.x, q0.y, q1.x, q1.y);
+              }
             }
           }
           fence_proxy_async_smem();
