@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ unpack
     // Work item = (input row, 8-sample quarter of the 32-sample chunk).
     const int tid = threadIdx.x;
-    constexpr int kUnpackThreads = 32 * kUnpackWarps;
+    static_assert(32 * kUnpackWarps == 8 * 64, "unpack threads = 64 rows x 8 sample groups");
     int s = 0, zs = 0;
     uint32_t ph = 0, zph = 0;
     bool ok = true;
@@ -246,41 +246,38 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!mbar_wait(b.z_empty + 8 * zs, zph ^ 1u, abort_flag, to)) { ok = false; break; }
           const uint8_t *pk = pk_buf + (size_t)s * p.pk_stage_bytes;
           uint8_t *zst = z_buf + (size_t)zs * p.z_stage_bytes;
+          // operand chunk `sub` of the packed stage (64 of its 128 samples)
           for (int r = 0; r < n_reg; ++r) {
             const XRegion rg = rgs[r];
-            const uint8_t *pkr = pk + rg.pk_off;
-            uint8_t *zr = zst + (size_t)rg.z_row * 128;
-            // work item = (input row, 8-sample group); 8 groups per 64-sample chunk
-            const int items = rg.n_in * 8;
-            // two work items per pass: their loads, decodes and stores interleave
-            for (int it0 = tid; it0 < items; it0 += 2 * kUnpackThreads) {
-              uint2 in[2];
-              int rowv[2], gv[2];
-              bool has[2];
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int it = it0 + h * kUnpackThreads;
-                has[h] = it < items;
-                rowv[h] = has[h] ? (it >> 3) : 0;
-                gv[h] = it & 7;
-                // packed rows arrive 128B-swizzled: 16-byte chunk c of row r sits at c ^ (r & 7)
-                const int c16 = (4 * sub + (gv[h] >> 1)) ^ (rowv[h] & 7);
-                in[h] = *reinterpret_cast<const uint2 *>(pkr + rowv[h] * kPackedRowBytes + c16 * 16 +
-                                                         (gv[h] & 1) * 8);
-              }
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                if (!has[h]) continue;
-                const int row = rowv[h];
-                const int rho = rg.interleaved ? (((row >> 3) << 4) | (row & 7)) : row;
-                uint8_t *pa = zr + (size_t)rho * 128;
-                const int off = (gv[h] ^ (row & 7)) << 4;
-                uint2 a0, q0, a1, q1;
-                decode_word(in[h].x, a0, q0);
-                decode_word(in[h].y, a1, q1);
-                *reinterpret_cast<uint4 *>(pa + off) = make_uint4(a0.x, a0.y, a1.x, a1.y);
+            // Thread tid owns rows row0 + 64 k (k = 0 .. n_in / 64 - 1) and the
+            // 8-sample group gv of each: its swizzle phase, group and store
+            // offsets are the same for all of its rows.
+            const int row0 = tid >> 3, gv = tid & 7, sw = row0 & 7;
+            // packed rows arrive 128B-swizzled: 16-byte chunk c of row r sits at c ^ (r & 7)
+            const uint8_t *src = pk + rg.pk_off + row0 * kPackedRowBytes +
+                                 (((4 * sub + (gv >> 1)) ^ sw) << 4) + (gv & 1) * 8;
+            const int rho0 = rg.interleaved ? (((row0 >> 3) << 4) | sw) : row0;
+            uint8_t *dst = zst + (size_t)(rg.z_row + rho0) * 128 + ((gv ^ sw) << 4);
+            const int dst_step = (rg.interleaved ? 128 : 64) * 128;  // 64 rows further on
+            const int n_k = rg.n_in >> 6;
+            for (int k = 0; k < n_k; k += 2) {
+              const bool two = k + 1 < n_k;
+              const uint2 in0 = *reinterpret_cast<const uint2 *>(src + k * 64 * kPackedRowBytes);
+              const uint2 in1 = two ? *reinterpret_cast<const uint2 *>(src + (k + 1) * 64 * kPackedRowBytes)
+                                    : in0;
+              uint2 a0, q0, a1, q1, a2, q2, a3, q3;
+              decode_word(in0.x, a0, q0);
+              decode_word(in0.y, a1, q1);
+              decode_word(in1.x, a2, q2);
+              decode_word(in1.y, a3, q3);
+              uint8_t *d0 = dst + k * dst_step;
+              *reinterpret_cast<uint4 *>(d0) = make_uint4(a0.x, a0.y, a1.x, a1.y);
+              if (rg.interleaved) *reinterpret_cast<uint4 *>(d0 + 8 * 128) = make_uint4(q0.x, q0.y, q1.x, q1.y);
+              if (two) {
+                uint8_t *d1 = d0 + dst_step;
+                *reinterpret_cast<uint4 *>(d1) = make_uint4(a2.x, a2.y, a3.x, a3.y);
                 if (rg.interleaved)
-                  *reinterpret_cast<uint4 *>(pa + 8 * 128 + off) = make_uint4(q0.x, q0.y, q1.x, q1.y);
+                  *reinterpret_cast<uint4 *>(d1 + 8 * 128) = make_uint4(q2.x, q2.y, q3.x, q3.y);
               }
             }
           }
