@@ -14,16 +14,16 @@
 // accumulation is exact; the
 // partials are folded into the int64 integration buffer once per launch.
 //
-// Kernel structure (persistent, one CTA per SM, 25 warps):
-//   warp 20     TMA producer: packed bytes [channel][input][time] -> smem ring
-//   warps 0-15  unpack: 4-bit nibbles -> E5M2 A/Q rows in the 128B-swizzled
+// Kernel structure (persistent, one CTA per SM, 17 warps):
+//   warp 12     TMA producer: packed bytes [channel][input][time] -> smem ring
+//   warps 0-7   unpack: 4-bit nibbles -> E5M2 A/Q rows in the 128B-swizzled
 //               K-major layout the MMA reads (the paper's CPU "fluff" step,
 //               Sec. 2.3, moved on chip)
-//   warps 21-24 MMA issuers: tcgen05.mma M=128 (64 inputs' A rows + Q rows),
+//   warps 13-16 MMA issuers: tcgen05.mma M=128 (64 inputs' A rows + Q rows),
 //               N = columns of the triangle strip, K = 32 per instruction;
 //               one issuing thread per accumulator, because a single thread
 //               issues an MMA only every ~200 cycles whatever its size
-//   warps 16-19 epilogue: tcgen05.ld of the fp32 accumulators, exchange of
+//   warps 8-11  epilogue: tcgen05.ld of the fp32 accumulators, exchange of
 //               re/im between lanes, int64 red.add into the lower triangle
 // A launch integrates up to kMaxBlocksPerLaunch blocks before the fold, as
 // long as the samples per fold keep every fp32 partial below 2^24.
@@ -88,7 +88,7 @@ __device__ __forceinline__ void red_add_s64(int64_t *addr, long long v) {
 
 }  // namespace
 
-// kThreads = 32 * 25: warps 0-15 unpack, 16-19 epilogue, 20 TMA, 21-24 MMA.
+// kThreads = 32 * 17: warps 0-7 unpack, 8-11 epilogue, 12 TMA, 13-16 MMA.
 __global__ void __launch_bounds__(kThreads, 1)
     xengine_cmac_kernel(const __grid_constant__ XMaps maps, const XParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ unpack
     // Work item = (input row, 8-sample quarter of the 32-sample chunk).
     const int tid = threadIdx.x;
-    static_assert(32 * kUnpackWarps == 8 * 64, "unpack threads = 64 rows x 8 sample groups");
+    static_assert(32 * kUnpackWarps == 4 * 64, "unpack threads = 64 rows x 4 sample groups");
     int s = 0, zs = 0;
     uint32_t ph = 0, zph = 0;
     bool ok = true;
@@ -250,34 +250,31 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int r = 0; r < n_reg; ++r) {
             const XRegion rg = rgs[r];
             // Thread tid owns rows row0 + 64 k (k = 0 .. n_in / 64 - 1) and the
-            // 8-sample group gv of each: its swizzle phase, group and store
-            // offsets are the same for all of its rows.
-            const int row0 = tid >> 3, gv = tid & 7, sw = row0 & 7;
+            // 16-sample group g of each; the 8 lanes of a quarter-warp share g
+            // and take 8 consecutive rows, so their swizzled 16-byte accesses
+            // fall on 8 different bank groups.
+            const int g = (tid >> 3) & 3, row0 = (tid & 7) | ((tid >> 5) << 3), sw = row0 & 7;
             // packed rows arrive 128B-swizzled: 16-byte chunk c of row r sits at c ^ (r & 7)
-            const uint8_t *src = pk + rg.pk_off + row0 * kPackedRowBytes +
-                                 (((4 * sub + (gv >> 1)) ^ sw) << 4) + (gv & 1) * 8;
+            const uint8_t *src = pk + rg.pk_off + row0 * kPackedRowBytes + (((4 * sub + g) ^ sw) << 4);
             const int rho0 = rg.interleaved ? (((row0 >> 3) << 4) | sw) : row0;
-            uint8_t *dst = zst + (size_t)(rg.z_row + rho0) * 128 + ((gv ^ sw) << 4);
+            uint8_t *dst = zst + (size_t)(rg.z_row + rho0) * 128;
+            const int off0 = ((2 * g) ^ sw) << 4, off1 = ((2 * g + 1) ^ sw) << 4;
             const int dst_step = (rg.interleaved ? 128 : 64) * 128;  // 64 rows further on
             const int n_k = rg.n_in >> 6;
-            for (int k = 0; k < n_k; k += 2) {
-              const bool two = k + 1 < n_k;
-              const uint2 in0 = *reinterpret_cast<const uint2 *>(src + k * 64 * kPackedRowBytes);
-              const uint2 in1 = two ? *reinterpret_cast<const uint2 *>(src + (k + 1) * 64 * kPackedRowBytes)
-                                    : in0;
+#pragma unroll 2
+            for (int k = 0; k < n_k; ++k) {
+              const uint4 in = *reinterpret_cast<const uint4 *>(src + k * 64 * kPackedRowBytes);
               uint2 a0, q0, a1, q1, a2, q2, a3, q3;
-              decode_word(in0.x, a0, q0);
-              decode_word(in0.y, a1, q1);
-              decode_word(in1.x, a2, q2);
-              decode_word(in1.y, a3, q3);
-              uint8_t *d0 = dst + k * dst_step;
-              *reinterpret_cast<uint4 *>(d0) = make_uint4(a0.x, a0.y, a1.x, a1.y);
-              if (rg.interleaved) *reinterpret_cast<uint4 *>(d0 + 8 * 128) = make_uint4(q0.x, q0.y, q1.x, q1.y);
-              if (two) {
-                uint8_t *d1 = d0 + dst_step;
-                *reinterpret_cast<uint4 *>(d1) = make_uint4(a2.x, a2.y, a3.x, a3.y);
-                if (rg.interleaved)
-                  *reinterpret_cast<uint4 *>(d1 + 8 * 128) = make_uint4(q2.x, q2.y, q3.x, q3.y);
+              decode_word(in.x, a0, q0);
+              decode_word(in.y, a1, q1);
+              decode_word(in.z, a2, q2);
+              decode_word(in.w, a3, q3);
+              uint8_t *d = dst + k * dst_step;
+              *reinterpret_cast<uint4 *>(d + off0) = make_uint4(a0.x, a0.y, a1.x, a1.y);
+              *reinterpret_cast<uint4 *>(d + off1) = make_uint4(a2.x, a2.y, a3.x, a3.y);
+              if (rg.interleaved) {
+                *reinterpret_cast<uint4 *>(d + 8 * 128 + off0) = make_uint4(q0.x, q0.y, q1.x, q1.y);
+                *reinterpret_cast<uint4 *>(d + 8 * 128 + off1) = make_uint4(q2.x, q2.y, q3.x, q3.y);
               }
             }
           }
