@@ -155,6 +155,39 @@ int corr_check(corr_ctx *ctx, void *stream);
  */
 int corr_plan(int n_in, uint8_t *cover, int *n_units, long long *issued_cmacs);
 
+/*
+ * Visibilities of one block without any allocation.  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate
+ * device memory -- code inside a framework that owns the whole device memory
+ * pool, and code on a real-time path where the implicit synchronisation of
+ * cudaMalloc/cudaFree would stall queued work.
+ *
+ * Writes vis[c][i(i+1)/2 + j] = sum_t x[c][i][t] conj(x[c][j][t]) for one
+ * block (no integration across calls, no Stokes) into d_vis
+ * (int64[n_chan][P][2], overwritten), from d_block as for corr_push_block.
+ * The kernel's scratch memory (its tile schedule and status word) lives in a
+ * file-scope device array of CORR_STATIC_SCRATCH_BYTES that every GPU which
+ * loads the library holds until the process exits; the call allocates nothing
+ * on the device or the host.
+ *   - Limits: n_ant * n_pol <= CORR_STATIC_MAX_INPUTS, block_len a multiple of
+ *     16 (at most CORR_MAX_BLOCK_LEN); d_block and d_vis 16-byte aligned.
+ *     Anything else returns CORR_EINVAL before any work is enqueued.
+ *   - The first call on a device looks up the array's device address and the
+ *     device limits; make that first call before any stream capture.
+ *   - Every call shares the one array and leaves its contents behind: calls
+ *     whose work overlaps on the GPU (other streams, other host threads) race
+ *     on it; serialise them.
+ *   - A device-side wait that runs out leaves d_vis incomplete and cannot be
+ *     reported here (there is no context); callers that need that check use
+ *     corr_create / corr_check.
+ * Stream-ordered and asynchronous.  Errors: CORR_EINVAL, CORR_EARCH,
+ * CORR_ECUDA.
+ */
+#define CORR_STATIC_SCRATCH_BYTES 4096
+#define CORR_STATIC_MAX_INPUTS 256
+int corr_xcorr_static(const uint8_t *d_block, int n_ant, int n_pol, int n_chan, int block_len,
+                      int64_t *d_vis, void *stream);
+
 /* Number of kernel launches the context has enqueued (pushes and dumps). */
 long long corr_launch_count(const corr_ctx *ctx);
 

@@ -40,6 +40,7 @@ ABI = [
                          ctypes.POINTER(_ll)]),
     ("corr_check", _ci, [_vp, _vp]),
     ("corr_plan", _ci, [_ci, _vp, ctypes.POINTER(_ci), ctypes.POINTER(_ll)]),
+    ("corr_xcorr_static", _ci, [_vp, _ci, _ci, _ci, _ci, _vp, _vp]),
     ("corr_launch_count", _ll, [_vp]),
     ("corr_destroy", None, [_vp]),
     ("corr_strerror", ctypes.c_char_p, [_ci]),
@@ -94,6 +95,23 @@ def plan(n_in: int, with_cover: bool = False):
     _ck(load().corr_plan(n_in, cover.ctypes.data if with_cover else None, ctypes.byref(nu),
                          ctypes.byref(iss)), "corr_plan")
     return nu.value, iss.value, cover
+
+
+def xcorr_static(block, n_ant: int, n_pol: int, vis=None, stream=None):
+    """One block's visibilities through corr_xcorr_static (no allocation in the
+    library): block is a uint8[n_chan][n_inputs][block_len] CUDA tensor, vis an
+    int64[n_chan][P][2] CUDA tensor to overwrite (allocated here by torch if
+    not given, outside the library call)."""
+    import torch
+    n_chan, n_in, block_len = block.shape
+    if n_in != n_ant * n_pol or not (block.is_cuda and block.dtype == torch.uint8
+                                      and block.is_contiguous()):
+        raise ValueError("block must be a contiguous uint8 CUDA tensor [n_chan][n_inputs][block_len]")
+    if vis is None:
+        vis = torch.empty((n_chan, n_pairs(n_in), 2), dtype=torch.int64, device=block.device)
+    _ck(load().corr_xcorr_static(block.data_ptr(), n_ant, n_pol, n_chan, block_len, vis.data_ptr(),
+                                 _stream_handle(stream)), "corr_xcorr_static")
+    return vis
 
 
 def n_pairs(n_in: int) -> int:
