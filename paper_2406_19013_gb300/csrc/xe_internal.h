@@ -23,7 +23,7 @@ constexpr int kPackedRowBytes = kPkSamples;
 constexpr int kChunksPerPk = kPkSamples / kChunkSamples;
 // Warp roles (see xengine.cu): unpack, epilogue (one per TMEM lane quarter),
 // TMA producer, MMA issuers (one issue stream per accumulator).
-constexpr int kUnpackWarps = 8;
+constexpr int kUnpackWarps = 16;
 constexpr int kEpiWarps = 4;
 constexpr int kMmaWarps = 4;
 constexpr int kWarpEpi0 = kUnpackWarps;

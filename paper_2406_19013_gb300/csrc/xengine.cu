@@ -14,16 +14,16 @@
 // accumulation is exact; the
 // partials are folded into the int64 integration buffer once per launch.
 //
-// Kernel structure (persistent, one CTA per SM, 17 warps):
-//   warp 12     TMA producer: packed bytes [channel][input][time] -> smem ring
-//   warps 0-7   unpack: 4-bit nibbles -> E5M2 A/Q rows in the 128B-swizzled
+// Kernel structure (persistent, one CTA per SM, 25 warps):
+//   warp 20     TMA producer: packed bytes [channel][input][time] -> smem ring
+//   warps 0-15  unpack: 4-bit nibbles -> E5M2 A/Q rows in the 128B-swizzled
 //               K-major layout the MMA reads (the paper's CPU "fluff" step,
 //               Sec. 2.3, moved on chip)
-//   warps 13-16 MMA issuers: tcgen05.mma M=128 (64 inputs' A rows + Q rows),
+//   warps 21-24 MMA issuers: tcgen05.mma M=128 (64 inputs' A rows + Q rows),
 //               N = columns of the triangle strip, K = 32 per instruction;
 //               one issuing thread per accumulator, because a single thread
 //               issues an MMA only every ~200 cycles whatever its size
-//   warps 8-11  epilogue: tcgen05.ld of the fp32 accumulators, exchange of
+//   warps 16-19 epilogue: tcgen05.ld of the fp32 accumulators, exchange of
 //               re/im between lanes, int64 red.add into the lower triangle
 // A launch integrates up to kMaxBlocksPerLaunch blocks before the fold, as
 // long as the samples per fold keep every fp32 partial below 2^24.
@@ -88,7 +88,7 @@ __device__ __forceinline__ void red_add_s64(int64_t *addr, long long v) {
 
 }  // namespace
 
-// kThreads = 32 * 17: warps 0-7 unpack, 8-11 epilogue, 12 TMA, 13-16 MMA.
+// kThreads = 32 * 25: warps 0-15 unpack, 16-19 epilogue, 20 TMA, 21-24 MMA.
 __global__ void __launch_bounds__(kThreads, 1)
     xengine_cmac_kernel(const __grid_constant__ XMaps maps, const XParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -195,17 +195,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (long long w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++nu) {
         const XUnit *u = p.units + (int)(w / p.n_chan);
         const int n_seg = u->n_seg;
-        XSeg mine[kMaxSegs / kMmaWarps];
-        int n_mine = 0;
-        for (int sg = m; sg < n_seg; sg += kMmaWarps) mine[n_mine++] = u->seg[sg];
+        static_assert(kMaxSegs / kMmaWarps == 2, "two segments per issuer at most");
+        // the (at most two) segments this issuer owns, held in registers
+        XSeg mine0 = u->seg[m < n_seg ? m : 0], mine1 = u->seg[m + kMmaWarps < n_seg ? m + kMmaWarps : 0];
+        const int n_mine = (m < n_seg) + (m + kMmaWarps < n_seg);
         if (nu > 0 && !mbar_wait(b.acc_empty, (uint32_t)((nu - 1) & 1), abort_flag, to)) break;
         tc_fence_after();
         for (int k = 0; k < n_chunks; ++k) {
           if (!mbar_wait(b.z_full + 8 * zs, zph, abort_flag, to)) { ok = false; break; }
           tc_fence_after();
           const uint32_t zb = smem_u32(z_buf + (size_t)zs * p.z_stage_bytes);
-          for (int j = 0; j < n_mine; ++j) {
-            const XSeg &sgm = mine[j];
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            if (j >= n_mine) break;
+            const XSeg &sgm = j == 0 ? mine0 : mine1;
             const uint32_t idesc = idesc_e5m2_f32(128, sgm.n);
             const uint32_t a0 = zb + (uint32_t)sgm.a_zrow * 128u;
             const uint32_t b0 = zb + (uint32_t)sgm.b_zrow * 128u;
@@ -230,15 +233,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ unpack
     // Work item = (input row, 8-sample quarter of the 32-sample chunk).
     const int tid = threadIdx.x;
-    static_assert(32 * kUnpackWarps == 4 * 64, "unpack threads = 64 rows x 4 sample groups");
+    static_assert(kUnpackWarps >= 1, "unpack threads = 8 rows x 4 sample groups per warp");
     int s = 0, zs = 0;
     uint32_t ph = 0, zph = 0;
     bool ok = true;
     for (long long w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
       const XUnit *u = p.units + (int)(w / p.n_chan);
       const int n_reg = u->n_reg;
-      XRegion rgs[2];
-      for (int r = 0; r < n_reg; ++r) rgs[r] = u->reg[r];
+      // the (at most two) staged regions, held in registers
+      const XRegion rg0 = u->reg[0], rg1 = u->reg[n_reg > 1 ? 1 : 0];
       for (int blk = 0; blk < p.n_blocks && ok; ++blk) {
         for (int kb = 0; kb < p.chunks_per_block; ++kb) {
           const int sub = kb % kChunksPerPk;  // operand chunk within the packed stage
@@ -247,23 +250,26 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint8_t *pk = pk_buf + (size_t)s * p.pk_stage_bytes;
           uint8_t *zst = z_buf + (size_t)zs * p.z_stage_bytes;
           // operand chunk `sub` of the packed stage (64 of its 128 samples)
-          for (int r = 0; r < n_reg; ++r) {
-            const XRegion rg = rgs[r];
-            // Thread tid owns rows row0 + 64 k (k = 0 .. n_in / 64 - 1) and the
-            // 16-sample group g of each; the 8 lanes of a quarter-warp share g
-            // and take 8 consecutive rows, so their swizzled 16-byte accesses
-            // fall on 8 different bank groups.
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            if (r >= n_reg) break;
+            const XRegion &rg = r == 0 ? rg0 : rg1;
+            // Thread tid owns rows row0 + R k (R = 8 * kUnpackWarps rows per
+            // pass) and the 16-sample group g of each; the 8 lanes of a
+            // quarter-warp share g and take 8 consecutive rows, so their
+            // swizzled 16-byte accesses fall on 8 different bank groups.
+            constexpr int R = 8 * kUnpackWarps;
             const int g = (tid >> 3) & 3, row0 = (tid & 7) | ((tid >> 5) << 3), sw = row0 & 7;
             // packed rows arrive 128B-swizzled: 16-byte chunk c of row r sits at c ^ (r & 7)
             const uint8_t *src = pk + rg.pk_off + row0 * kPackedRowBytes + (((4 * sub + g) ^ sw) << 4);
             const int rho0 = rg.interleaved ? (((row0 >> 3) << 4) | sw) : row0;
             uint8_t *dst = zst + (size_t)(rg.z_row + rho0) * 128;
             const int off0 = ((2 * g) ^ sw) << 4, off1 = ((2 * g + 1) ^ sw) << 4;
-            const int dst_step = (rg.interleaved ? 128 : 64) * 128;  // 64 rows further on
-            const int n_k = rg.n_in >> 6;
+            const int dst_step = (rg.interleaved ? 2 * R : R) * 128;  // R rows further on
+            const int n_k = row0 < rg.n_in ? (rg.n_in - row0 + R - 1) / R : 0;
 #pragma unroll 2
             for (int k = 0; k < n_k; ++k) {
-              const uint4 in = *reinterpret_cast<const uint4 *>(src + k * 64 * kPackedRowBytes);
+              const uint4 in = *reinterpret_cast<const uint4 *>(src + k * R * kPackedRowBytes);
               uint2 a0, q0, a1, q1, a2, q2, a3, q3;
               decode_word(in.x, a0, q0);
               decode_word(in.y, a1, q1);
