@@ -16,9 +16,10 @@ autos, N(N+1)/2 per channel per sample), in Tera-CMAC/s, whole job.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-For N > 1 launch under torchrun: every rank correlates its own 1024-channel
-band (channels are independent, so there is no data-path collective) and the
-job value is the sum of CMACs over the slowest rank's time (weak scaling).
+For N > 1 launch under torchrun: rank r correlates channels
+[1024 r, 1024 (r + 1)) of one global band (channels are independent, so there
+is no data-path collective) and the job value is the sum of CMACs over the
+slowest rank's time (weak scaling).
 """
 from __future__ import annotations
 
@@ -198,7 +199,7 @@ def run_ours(args):
     import numpy as np
     import torch
 
-    from paper_2406_19013_gb300 import Correlator, build
+    from paper_2406_19013_gb300 import Correlator, build, shard
     from paper_2406_19013_gb300.corr import plan
     from synth import synth
 
@@ -212,14 +213,17 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     build.build()
 
-    # ---- inputs: a ring of distinct blocks, generated on the host in pinned memory
-    w = synth.workload("paper", seed=1 + rank)
+    # ---- inputs: a ring of distinct blocks, generated on the host in pinned
+    # memory; rank r holds channels [r*1024, (r+1)*1024) of one global band
+    w = synth.workload("paper", seed=1)
+    c0, n_band = shard.band(rank, ws, N_CHAN * ws)
+    assert n_band == N_CHAN
     ring_n = max(1, args.ring)
     t0 = time.perf_counter()
     host = []
     for r in range(ring_n):
         hb = torch.empty((N_CHAN, N_IN, BLOCK_LEN), dtype=torch.uint8, pin_memory=True)
-        w.block(r, n_chan=N_CHAN, out=hb.numpy())
+        w.block(r, c0=c0, n_chan=N_CHAN, out=hb.numpy())
         host.append(hb)
     log(f"[bench] rank {rank}: generated {ring_n} blocks in {time.perf_counter() - t0:.1f} s")
     ring = [hb.to(dev, non_blocking=False) for hb in host]
@@ -276,11 +280,7 @@ def run_ours(args):
     n_launch = xc.launch_count() - n0
     xc.check()
     elapsed_ms = start.elapsed_time(end)
-    t_max = elapsed_ms
-    if ws > 1:
-        tt = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = shard.max_over_ranks(elapsed_ms)
     cmacs = CMAC_PER_BLOCK * BLOCKS_PER_STEP * args.steps * ws
     value = cmacs / (t_max / 1e3) / 1e12
 
@@ -324,11 +324,7 @@ def run_ours(args):
         for s in range(args.e2e_steps):
             e2e_step(s)
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if ws > 1:
-            tt = torch.tensor([dt], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            dt = float(tt.item())
+        dt = shard.max_over_ranks(time.perf_counter() - t0)
         xe.check()
         xe.close()
         e2e = {"value": CMAC_PER_BLOCK * BLOCKS_PER_STEP * args.e2e_steps * ws / dt / 1e12,

@@ -229,6 +229,42 @@ def test_independent_contexts(corr, torch_cuda, oracle_mod, synth_mod):
         b.close()
 
 
+def test_channel_bands_on_two_streams(corr, torch_cuda, oracle_mod, synth_mod):
+    # The multi-GPU layout on one GPU: two contexts, each on its own stream,
+    # integrate the two bands of one workload; stitched, they equal the
+    # oracle over the whole band (and the Stokes of a whole-band context).
+    torch = torch_cuda
+    from paper_2406_19013_gb300 import shard
+    w = synth_mod.workload("tiny", seed=21)
+    n_chan, T = 37, 512
+    blocks = [synth_mod.make_block(w.n_in, n_chan, T, seed=21, block=b, tones=w.tones)
+              for b in range(2)]
+    want = oracle_mod.xcorr(blocks[0]) + oracle_mod.xcorr(blocks[1])
+    parts, parts_st = [], []
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    ctxs = []
+    try:
+        for r in range(2):
+            c0, n = shard.band(r, 2, n_chan)
+            xc = corr.Correlator(w.n_ant, w.n_pol, n, T)
+            ctxs.append(xc)
+            with torch.cuda.stream(streams[r]):
+                for b in blocks:
+                    xc.push_block(torch.from_numpy(np.ascontiguousarray(b[c0:c0 + n])).cuda(),
+                                  streams[r])
+                v, st = xc.dump(stream=streams[r])
+            parts.append(v)
+            parts_st.append(st)
+        torch.cuda.synchronize()
+        got = np.concatenate([v.cpu().numpy() for v in parts])
+        assert np.array_equal(got, want)
+        got_st = np.concatenate([s.cpu().numpy() for s in parts_st])
+        assert np.array_equal(got_st, oracle_mod.stokes(want, w.n_ant))
+    finally:
+        for xc in ctxs:
+            xc.close()
+
+
 def _autos_numpy(x):
     s = x.astype(np.int8)
     re = (s >> 4).astype(np.int64)
