@@ -155,6 +155,44 @@ int corr_check(corr_ctx *ctx, void *stream);
  */
 int corr_plan(int n_in, uint8_t *cover, int *n_units, long long *issued_cmacs);
 
+/* Triangle covers (the tile schedule's shape; see corr_plan_cover).
+ *   WINDOW: N <= 256.  Every unit stages all inputs once per chunk, and the
+ *           64-input row tiles' strips share it, packed into 512 TMEM columns.
+ *   STRIPS: N <= 256.  One unit per row tile t, staging inputs [0, 64(t+1)).
+ *   PAIRS:  any N.  Pairs of row tiles against 256-column pieces of their
+ *           strip; the cover used above 256 inputs.
+ * WINDOW and STRIPS fall back to PAIRS above 256 inputs. */
+#define CORR_COVER_WINDOW 0
+#define CORR_COVER_STRIPS 1
+#define CORR_COVER_PAIRS 2
+
+/* As corr_plan, for the given cover.  Errors: CORR_EINVAL (n_in out of
+ * range, unknown cover). */
+int corr_plan_cover(int n_in, int cover, uint8_t *cover_out, int *n_units,
+                    long long *issued_cmacs);
+
+/*
+ * Host-only view of how one launch's work is dealt to the GPU's
+ * multiprocessors (no device needed).
+ *   - A unit is (template, channel): one of the cover's n_units templates on
+ *     one channel, over all n_blocks blocks of block_len samples.
+ *   - Units are cut at 128-sample stage boundaries into items, and every CTA
+ *     (at most `grid`) runs a contiguous run of items of about equal
+ *     modelled cost.  That cost is the operand rows unpacked plus a fixed
+ *     fold cost per item.
+ *   - items, if not NULL, receives up to `cap` rows of 5 ints:
+ *     (problem = 0, template, channel, first stage, stages).  Stage k of the
+ *     launch is 128-sample stage k % ceil(block_len / 128) of block
+ *     k / ceil(block_len / 128).
+ *   - cta_first, if not NULL, receives grid + 1 ints: CTA b runs items
+ *     [cta_first[b], cta_first[b + 1]), for b < *used_grid.
+ *   - *n_items and *used_grid receive the totals.
+ * Errors: CORR_EINVAL (sizes out of range, unknown cover, or cap < *n_items
+ * with items given; *n_items is still set).
+ */
+int corr_plan_items(int n_in, int n_chan, int block_len, int n_blocks, int cover, int grid,
+                    int *items, int cap, int *n_items, int *cta_first, int *used_grid);
+
 /*
  * Visibilities of one block without any allocation.  The paper has no
  * counterpart: this entry point exists for callers that must not allocate
@@ -190,6 +228,72 @@ int corr_xcorr_static(const uint8_t *d_block, int n_ant, int n_pol, int n_chan, 
 
 /* Number of kernel launches the context has enqueued (pushes and dumps). */
 long long corr_launch_count(const corr_ctx *ctx);
+
+/*
+ * Batches: many independent correlators in shared launches.
+ *
+ * The paper's system runs one X-engine per server and pipeline instance,
+ * each on its own array (Sec. 2.2-2.3).  A batch holds n_inst such
+ * correlators, each with its own n_ant, n_pol, n_chan and block_len.
+ *   - Each instance has its own int64 integration buffer, sized and laid out
+ *     as a context's.
+ *   - One corr_batch_push integrates one block of every instance.
+ *   - The units of all instances are dealt to the multiprocessors of one
+ *     persistent launch per shared-memory layout, so instances with few
+ *     channels fill the gaps left by large ones.
+ *   - With CORR_BATCH_AUTOTUNE, each distinct (input count, block length
+ *     rounded up to a power of two) gets its triangle cover by timing one
+ *     launch of every candidate cover on a synthetic problem of that size.
+ *     The choice is cached for the process.
+ *   - Results are bit-identical to one context per instance: every sum is
+ *     an exact integer.
+ */
+#define CORR_BATCH_AUTOTUNE 1
+typedef struct corr_batch corr_batch;
+
+/* Creates the batch: arrays of n_inst sizes (as for corr_create).
+ * Allocates every integration buffer (zeroed) on the current device.
+ * Errors: CORR_EINVAL (any size as for corr_create, unknown flag, NULL
+ * array), CORR_EARCH, CORR_ENOMEM, CORR_ECUDA, CORR_ETIMEOUT (while tuning). */
+int corr_batch_create(int n_inst, const int *n_ant, const int *n_pol, const int *n_chan,
+                      const int *block_len, int flags, corr_batch **out);
+
+/* Integrates one block of every instance.  d_blocks is a host array of n_inst
+ * device pointers, instance k's block laid out as for corr_push_block with
+ * that instance's sizes, 16-byte aligned.  Stream-ordered and asynchronous;
+ * the blocks must stay unchanged until the stream has executed the call.
+ * The pointer array may be reused at once.
+ * Errors: CORR_EINVAL (NULL batch or array, a NULL or misaligned pointer;
+ * nothing is enqueued), CORR_ECUDA. */
+int corr_batch_push(corr_batch *b, const uint8_t *const *d_blocks, void *stream);
+
+/* As corr_dump, for instance `inst` alone (its buffer is zeroed; the others
+ * keep integrating).  Errors: CORR_EINVAL (inst out of range, d_stokes with
+ * n_pol == 1, misaligned pointer), CORR_ECUDA. */
+int corr_batch_dump(corr_batch *b, int inst, int64_t *d_vis, int64_t *d_stokes, void *stream);
+
+/* As corr_sizes, for instance `inst`.  Errors: CORR_EINVAL. */
+int corr_batch_sizes(const corr_batch *b, int inst, size_t *vis_elems, size_t *stokes_elems,
+                     long long *samples_integrated);
+
+/* Instance `inst`'s cover (CORR_COVER_*), its launch group, and the number of
+ * launch groups (one CMAC launch each per push).  Any output may be NULL.
+ * Errors: CORR_EINVAL. */
+int corr_batch_info(const corr_batch *b, int inst, int *cover, int *group, int *n_groups);
+
+/* As corr_check, for the batch's device status word. */
+int corr_batch_check(corr_batch *b, void *stream);
+
+/* Kernel launches the batch has enqueued (pushes and dumps). */
+long long corr_batch_launch_count(const corr_batch *b);
+
+/* Releases the batch.  The caller must have synchronised its streams.  NULL
+ * is ignored. */
+void corr_batch_destroy(corr_batch *b);
+
+/* The autotuner's cached cover for (n_in, block_len), or -1 if none is cached
+ * yet.  Host-only.  Errors: CORR_EINVAL (non-positive size). */
+int corr_tuned_cover(int n_in, int block_len);
 
 /* Releases everything the context owns.  The caller must have synchronised
  * every stream that used it.  NULL is ignored. */

@@ -26,6 +26,10 @@ CORR_ETIMEOUT = -5
 CORR_ESTATE = -6
 CORR_MAX_BLOCK_LEN = 131071
 CORR_MAX_INPUTS = 8192
+CORR_COVER_WINDOW = 0
+CORR_COVER_STRIPS = 1
+CORR_COVER_PAIRS = 2
+CORR_BATCH_AUTOTUNE = 1
 
 # (name, restype, argtypes) of every function include/corr.h declares
 _vp, _ci, _ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
@@ -40,6 +44,20 @@ ABI = [
                          ctypes.POINTER(_ll)]),
     ("corr_check", _ci, [_vp, _vp]),
     ("corr_plan", _ci, [_ci, _vp, ctypes.POINTER(_ci), ctypes.POINTER(_ll)]),
+    ("corr_plan_cover", _ci, [_ci, _ci, _vp, ctypes.POINTER(_ci), ctypes.POINTER(_ll)]),
+    ("corr_plan_items", _ci, [_ci, _ci, _ci, _ci, _ci, _ci, _vp, _ci, ctypes.POINTER(_ci), _vp,
+                              ctypes.POINTER(_ci)]),
+    ("corr_batch_create", _ci, [_ci, _vp, _vp, _vp, _vp, _ci, ctypes.POINTER(_vp)]),
+    ("corr_batch_push", _ci, [_vp, ctypes.POINTER(_vp), _vp]),
+    ("corr_batch_dump", _ci, [_vp, _ci, _vp, _vp, _vp]),
+    ("corr_batch_sizes", _ci, [_vp, _ci, ctypes.POINTER(ctypes.c_size_t),
+                               ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_ll)]),
+    ("corr_batch_info", _ci, [_vp, _ci, ctypes.POINTER(_ci), ctypes.POINTER(_ci),
+                              ctypes.POINTER(_ci)]),
+    ("corr_batch_check", _ci, [_vp, _vp]),
+    ("corr_batch_launch_count", _ll, [_vp]),
+    ("corr_batch_destroy", None, [_vp]),
+    ("corr_tuned_cover", _ci, [_ci, _ci]),
     ("corr_xcorr_static", _ci, [_vp, _ci, _ci, _ci, _ci, _vp, _vp]),
     ("corr_launch_count", _ll, [_vp]),
     ("corr_destroy", None, [_vp]),
@@ -95,6 +113,39 @@ def plan(n_in: int, with_cover: bool = False):
     _ck(load().corr_plan(n_in, cover.ctypes.data if with_cover else None, ctypes.byref(nu),
                          ctypes.byref(iss)), "corr_plan")
     return nu.value, iss.value, cover
+
+
+def plan_cover(n_in: int, cover: int, with_cover: bool = False):
+    """As ``plan`` for the given CORR_COVER_* cover."""
+    out = np.zeros((n_in, n_in), dtype=np.uint8) if with_cover else None
+    nu, iss = _ci(), _ll()
+    _ck(load().corr_plan_cover(n_in, cover, out.ctypes.data if with_cover else None,
+                               ctypes.byref(nu), ctypes.byref(iss)), "corr_plan_cover")
+    return nu.value, iss.value, out
+
+
+def plan_items(n_in: int, n_chan: int, block_len: int, n_blocks: int, grid: int,
+               cover: int = CORR_COVER_WINDOW):
+    """The per-CTA item split of one launch: (items int32[n][5] as (problem,
+    template, channel, first stage, stages), cta_first int32[used_grid + 1])."""
+    lib = load()
+    n, used = _ci(), _ci()
+    _ck(lib.corr_plan_items(n_in, n_chan, block_len, n_blocks, cover, grid, None, 0,
+                            ctypes.byref(n), None, ctypes.byref(used)), "corr_plan_items")
+    items = np.zeros((n.value, 5), dtype=np.int32)
+    first = np.zeros(grid + 1, dtype=np.int32)
+    _ck(lib.corr_plan_items(n_in, n_chan, block_len, n_blocks, cover, grid, items.ctypes.data,
+                            n.value, ctypes.byref(n), first.ctypes.data, ctypes.byref(used)),
+        "corr_plan_items")
+    return items, first[:used.value + 1]
+
+
+def tuned_cover(n_in: int, block_len: int) -> int:
+    """The autotuner's cached cover for (n_in, block_len), or -1."""
+    rc = load().corr_tuned_cover(n_in, block_len)
+    if rc < -1:
+        _ck(rc, "corr_tuned_cover")
+    return rc
 
 
 def xcorr_static(block, n_ant: int, n_pol: int, vis=None, stream=None):
@@ -228,6 +279,98 @@ class Correlator:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.corr_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent correlators integrated by shared launches (corr_batch_*).
+
+    ``shapes`` is a list of (n_ant, n_pol, n_chan, block_len).  ``push``
+    takes one uint8[n_chan][n_inputs][block_len] CUDA tensor per instance;
+    ``dump(k)`` returns instance k's (vis, stokes or None) and restarts its
+    integration.
+    """
+
+    def __init__(self, shapes, autotune: bool = False):
+        self._lib = load()
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        n = len(self.shapes)
+        arr = [np.array([sh[k] for sh in self.shapes], dtype=np.int32) for k in range(4)]
+        h = _vp()
+        _ck(self._lib.corr_batch_create(n, *(a.ctypes.data for a in arr),
+                                        CORR_BATCH_AUTOTUNE if autotune else 0, ctypes.byref(h)),
+            "corr_batch_create")
+        self._h = h
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def push(self, blocks, stream=None):
+        import torch
+        if len(blocks) != len(self.shapes):
+            raise ValueError("one block per instance")
+        ptrs = []
+        for blk, (na, npol, nc, T) in zip(blocks, self.shapes):
+            if isinstance(blk, torch.Tensor):
+                if not (blk.is_cuda and blk.dtype == torch.uint8 and blk.is_contiguous()
+                        and blk.numel() == nc * na * npol * T):
+                    raise ValueError("each block must be a contiguous uint8 CUDA tensor of its "
+                                     "instance's size")
+                ptrs.append(blk.data_ptr())
+            else:
+                ptrs.append(int(blk))
+        arr = (_vp * len(ptrs))(*ptrs)
+        _ck(self._lib.corr_batch_push(self._h, arr, _stream_handle(stream)), "corr_batch_push")
+
+    def dump(self, k: int, vis=None, stokes=None, want_stokes: bool | None = None, stream=None):
+        import torch
+        na, npol, nc, _ = self.shapes[k]
+        if want_stokes is None:
+            want_stokes = npol == 2
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if vis is None:
+            vis = torch.empty((nc, n_pairs(na * npol), 2), dtype=torch.int64, device=dev)
+        if stokes is None and want_stokes:
+            stokes = torch.empty((nc, n_pairs(na), 4, 2), dtype=torch.int64, device=dev)
+        _ck(self._lib.corr_batch_dump(self._h, k, vis.data_ptr(),
+                                      stokes.data_ptr() if stokes is not None else None,
+                                      _stream_handle(stream)), "corr_batch_dump")
+        return vis, stokes
+
+    def info(self, k: int):
+        """(cover, launch group, number of launch groups) of instance k."""
+        cv, g, ng = _ci(), _ci(), _ci()
+        _ck(self._lib.corr_batch_info(self._h, k, ctypes.byref(cv), ctypes.byref(g),
+                                      ctypes.byref(ng)), "corr_batch_info")
+        return cv.value, g.value, ng.value
+
+    def samples_integrated(self, k: int) -> int:
+        s = _ll()
+        _ck(self._lib.corr_batch_sizes(self._h, k, None, None, ctypes.byref(s)),
+            "corr_batch_sizes")
+        return s.value
+
+    def check(self, stream=None):
+        _ck(self._lib.corr_batch_check(self._h, _stream_handle(stream)), "corr_batch_check")
+
+    def launch_count(self) -> int:
+        return int(self._lib.corr_batch_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.corr_batch_destroy(self._h)
             self._h = None
 
     def __enter__(self):

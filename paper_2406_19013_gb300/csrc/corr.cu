@@ -11,12 +11,20 @@
 #include <vector>
 
 #include "corr.h"
+#include "sched.h"
 #include "xe_internal.h"
 
 using xe::XParams;
-using xe::XRegion;
 using xe::XSeg;
 using xe::XUnit;
+
+// Device copy of a launch's item split (see sched.h), one per number of
+// blocks per launch.
+struct ItemPlan {
+  xe::XItem *d_items;
+  int *d_cta_first;
+  int grid;
+};
 
 struct corr_ctx {
   int n_ant, n_pol, n_chan, block_len, n_in;
@@ -25,7 +33,10 @@ struct corr_ctx {
   int64_t *d_acc;
   int *d_status;
   XUnit *d_units;
+  xe::XProb *d_prob;
   int n_tpl;
+  int per_launch;  // blocks per CMAC launch (<= kMaxBlocksPerLaunch)
+  ItemPlan plans[xe::kMaxBlocksPerLaunch + 1];
   int smem_bytes, z_stages, pk_stages;
   uint32_t z_stage_bytes, pk_stage_bytes;
   int pitch;           // row pitch of the staged block (block_len rounded up to 16)
@@ -43,107 +54,7 @@ struct corr_ctx {
 
 namespace {
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn get_encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
-
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
-
-// Tiles of 64 inputs (rows) cover the lower triangle strip by strip: row tile
-// t needs columns [0, min(64(t+1), N)).  Columns are staged once per chunk
-// and shared by all row tiles of a unit.
-std::vector<XUnit> build_schedule(int N) {
-  std::vector<XUnit> units;
-  const int n16 = round_up(N, 16);
-  const int n_rt = (N + xe::kTileInputs - 1) / xe::kTileInputs;
-  auto add_seg = [](XUnit &u, int a_zrow, int b_zrow, int b_sbo, int n, int row_in0, int col_in0) {
-    XSeg &s = u.seg[u.n_seg];
-    int col = 0;
-    for (int k = 0; k < u.n_seg; ++k) col += u.seg[k].n;
-    s.a_zrow = a_zrow; s.b_zrow = b_zrow; s.b_sbo = b_sbo; s.n = n; s.tmem_col = col;
-    s.row_in0 = row_in0; s.col_in0 = col_in0;
-    u.n_seg++;
-    u.work += n;
-  };
-  auto add_reg = [](XUnit &u, int in_lo, int n_in, int interleaved) {
-    XRegion &r = u.reg[u.n_reg];
-    r.in_lo = in_lo; r.n_in = n_in; r.interleaved = interleaved;
-    r.z_row = u.z_rows; r.pk_off = u.pk_bytes;
-    u.z_rows += interleaved ? 2 * n_in : n_in;
-    u.pk_bytes += n_in * xe::kPackedRowBytes;
-    u.n_reg++;
-  };
-  if (N <= 256) {
-    // one staged window [0, 64 n_rt); strips packed first-fit into 512 TMEM columns
-    std::vector<int> tiles(n_rt);
-    for (int t = 0; t < n_rt; ++t) tiles[t] = t;
-    std::sort(tiles.begin(), tiles.end(), [](int a, int b) { return a > b; });
-    std::vector<std::vector<int>> bins;
-    std::vector<int> used;
-    for (int t : tiles) {
-      const int n = std::min(xe::kTileInputs * (t + 1), n16);
-      bool placed = false;
-      for (size_t k = 0; k < bins.size(); ++k)
-        if (used[k] + n <= xe::kTmemCols) { bins[k].push_back(t); used[k] += n; placed = true; break; }
-      if (!placed) { bins.push_back({t}); used.push_back(n); }
-    }
-    for (auto &bin : bins) {
-      XUnit u;
-      std::memset(&u, 0, sizeof(u));
-      int t_max = 0;
-      for (int t : bin) t_max = std::max(t_max, t);
-      add_reg(u, 0, xe::kTileInputs * (t_max + 1), 1);
-      for (int t : bin)
-        add_seg(u, 128 * t, 0, 2048, std::min(xe::kTileInputs * (t + 1), n16),
-                xe::kTileInputs * t, 0);
-      units.push_back(u);
-    }
-  } else {
-    // pairs of row tiles (2m, 2m+1) against 256-column pieces of their strip
-    for (int m = 0; 2 * m < n_rt; ++m) {
-      const int t0 = 2 * m;
-      const bool two = t0 + 1 < n_rt;
-      const int row_lo = xe::kTileInputs * t0;
-      const int kd = row_lo / 256;  // piece holding the diagonal
-      for (int k = 0; k <= kd; ++k) {
-        XUnit u;
-        std::memset(&u, 0, sizeof(u));
-        if (k < kd) {
-          add_reg(u, row_lo, two ? 128 : 64, 1);
-          add_reg(u, 256 * k, 256, 0);
-          const int bz = u.reg[1].z_row;
-          add_seg(u, 0, bz, 1024, 256, row_lo, 256 * k);
-          if (two) add_seg(u, 128, bz, 1024, 256, row_lo + 64, 256 * k);
-        } else {
-          const int lo = 256 * k;
-          const int hi = row_lo + (two ? 128 : 64);
-          add_reg(u, lo, hi - lo, 1);
-          const int a0 = 2 * (row_lo - lo);
-          add_seg(u, a0, 0, 2048, std::min(row_lo + 64, n16) - lo, row_lo, lo);
-          if (two) add_seg(u, a0 + 128, 0, 2048, std::min(row_lo + 128, n16) - lo, row_lo + 64, lo);
-        }
-        units.push_back(u);
-      }
-    }
-  }
-  std::stable_sort(units.begin(), units.end(),
-                   [](const XUnit &a, const XUnit &b) { return a.work > b.work; });
-  return units;
-}
 
 int cuda_err(cudaError_t e) {
   if (e == cudaSuccess) return CORR_OK;
@@ -152,18 +63,9 @@ int cuda_err(cudaError_t e) {
 }
 
 int encode_block_map(const corr_ctx *ctx, const void *base, CUtensorMap *m) {
-  EncodeTiledFn enc = get_encode_fn();
-  if (!enc) return CORR_ECUDA;
-  const cuuint64_t dims[3] = {(cuuint64_t)ctx->block_len, (cuuint64_t)ctx->n_in,
-                              (cuuint64_t)ctx->n_chan};
-  const cuuint64_t strides[2] = {(cuuint64_t)ctx->pitch,
-                                 (cuuint64_t)ctx->pitch * (cuuint64_t)ctx->n_in};
-  const cuuint32_t box[3] = {(cuuint32_t)xe::kPkSamples, (cuuint32_t)xe::kTileInputs, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(base), dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? CORR_OK : CORR_ECUDA;
+  return xe::encode_block_map(base, ctx->block_len, ctx->n_in, ctx->n_chan, ctx->pitch, m)
+             ? CORR_OK
+             : CORR_ECUDA;
 }
 
 int free_ctx(corr_ctx *ctx) {
@@ -171,6 +73,11 @@ int free_ctx(corr_ctx *ctx) {
   cudaFree(ctx->d_acc);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_units);
+  cudaFree(ctx->d_prob);
+  for (auto &pl : ctx->plans) {
+    cudaFree(pl.d_items);
+    cudaFree(pl.d_cta_first);
+  }
   cudaFree(ctx->d_pitched);
   for (int k = 0; k < 2; ++k) {
     cudaFree(ctx->d_stage[k]);
@@ -242,34 +149,21 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
     if (ms > 0) ctx->timeout_ns = (unsigned long long)ms * 1000000ull;
   }
 
-  std::vector<XUnit> units = build_schedule(ctx->n_in);
+  std::vector<XUnit> units = xe::build_schedule(ctx->n_in);
   ctx->n_tpl = (int)units.size();
-  int max_z = 0, max_pk = 0;
-  for (const XUnit &u : units) {
-    max_z = std::max(max_z, u.z_rows);
-    max_pk = std::max(max_pk, u.pk_bytes);
-  }
-  ctx->z_stage_bytes = (uint32_t)round_up(max_z * 128, 1024);
-  ctx->pk_stage_bytes = (uint32_t)round_up(max_pk, 1024);  // swizzled TMA destination
-  const int fixed = 1024 /* alignment slack */ + 256 /* barriers, TMEM address, flags */;
-  static_assert(8 * (2 * 4 + 2 * 4 + 2 + xe::kMmaWarps) + 8 <= 256, "barrier area");
-  // three packed stages (bytes in flight for HBM) if that leaves two or more
-  // operand stages, else two
-  int zs = 0;
-  for (int ps = 3; ps >= 2 && zs < 2; --ps) {
-    ctx->pk_stages = ps;
-    zs = (smem_optin - fixed - ps * (int)ctx->pk_stage_bytes) / (int)ctx->z_stage_bytes;
-  }
-  zs = std::min(zs, 4);
-  if (zs < 2) {
+  xe::StageLayout L;
+  if (!xe::stage_layout({&units}, smem_optin, 4, &L)) {
     free_ctx(ctx);
     return CORR_EINVAL;
   }
-  ctx->z_stages = zs;
-  ctx->smem_bytes = fixed + zs * (int)ctx->z_stage_bytes + ctx->pk_stages * (int)ctx->pk_stage_bytes;
-  // one CTA per SM: the kernel holds all 512 TMEM columns
-  ctx->smem_bytes = std::max(ctx->smem_bytes, smem_optin / 2 + 1024);
-  ctx->smem_bytes = std::min(ctx->smem_bytes, smem_optin);
+  ctx->z_stages = L.z_stages;
+  ctx->pk_stages = L.pk_stages;
+  ctx->z_stage_bytes = L.z_stage_bytes;
+  ctx->pk_stage_bytes = L.pk_stage_bytes;
+  ctx->smem_bytes = L.smem_bytes;
+  // a fold must come before 2^24 / 128 samples have been accumulated in fp32
+  ctx->per_launch = std::max(1, std::min(xe::kMaxBlocksPerLaunch, CORR_MAX_BLOCK_LEN / block_len));
+  if (ctx->pitch != block_len) ctx->per_launch = 1;  // one pitched staging buffer
 
   int rc = CORR_OK;
   const size_t acc_bytes = (size_t)n_chan * (size_t)ctx->n_pairs * 16;
@@ -286,18 +180,44 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
       return rc;
     }
   }
+  // the problem descriptor and the balanced item split for every launch size
+  xe::XProb prob;
+  prob.units = ctx->d_units;
+  prob.acc = ctx->d_acc;
+  prob.n_pairs = ctx->n_pairs;
+  prob.n_in = ctx->n_in;
+  prob.chunks_per_block = (block_len + xe::kChunkSamples - 1) / xe::kChunkSamples;
+  prob.pk_per_block = (block_len + xe::kPkSamples - 1) / xe::kPkSamples;
+  prob.map0 = 0;
+  if ((rc = cuda_err(cudaMalloc(&ctx->d_prob, sizeof(prob)))) != CORR_OK ||
+      (rc = cuda_err(cudaMemcpy(ctx->d_prob, &prob, sizeof(prob), cudaMemcpyHostToDevice))) !=
+          CORR_OK) {
+    free_ctx(ctx);
+    return rc;
+  }
+  for (int nb = 1; nb <= ctx->per_launch; ++nb) {
+    std::vector<xe::XItem> items;
+    std::vector<int> first;
+    ItemPlan &pl = ctx->plans[nb];
+    pl.grid = xe::build_items({{&units, n_chan, block_len, nb}}, ctx->n_sm, items, first);
+    if ((rc = cuda_err(cudaMalloc(&pl.d_items, items.size() * sizeof(xe::XItem)))) != CORR_OK ||
+        (rc = cuda_err(cudaMalloc(&pl.d_cta_first, first.size() * sizeof(int)))) != CORR_OK ||
+        (rc = cuda_err(cudaMemcpy(pl.d_items, items.data(), items.size() * sizeof(xe::XItem),
+                                  cudaMemcpyHostToDevice))) != CORR_OK ||
+        (rc = cuda_err(cudaMemcpy(pl.d_cta_first, first.data(), first.size() * sizeof(int),
+                                  cudaMemcpyHostToDevice))) != CORR_OK) {
+      free_ctx(ctx);
+      return rc;
+    }
+  }
   if ((rc = cuda_err(cudaMemset(ctx->d_acc, 0, acc_bytes))) != CORR_OK ||
       (rc = cuda_err(cudaMemset(ctx->d_status, 0, sizeof(int)))) != CORR_OK ||
       (rc = cuda_err(cudaMemcpy(ctx->d_units, units.data(), units.size() * sizeof(XUnit),
                                 cudaMemcpyHostToDevice))) != CORR_OK ||
-      (rc = cuda_err(xe::cmac_set_smem(ctx->smem_bytes))) != CORR_OK ||
+      (rc = cuda_err(xe::cmac_set_smem(smem_optin))) != CORR_OK ||
       (rc = cuda_err(cudaDeviceSynchronize())) != CORR_OK) {
     free_ctx(ctx);
     return rc;
-  }
-  if (!get_encode_fn()) {
-    free_ctx(ctx);
-    return CORR_ECUDA;
   }
   *out = ctx;
   return CORR_OK;
@@ -310,27 +230,16 @@ int corr_push_blocks(corr_ctx *ctx, const uint8_t *const *d_blocks, int n_blocks
     if (!d_blocks[k] || (reinterpret_cast<uintptr_t>(d_blocks[k]) & 15u) != 0) return CORR_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   static_assert(sizeof(CUtensorMap) == sizeof(xe::XMaps::m[0]), "tensor map size");
-  // a fold must come before 2^24 / 128 samples have been accumulated in fp32
-  int per = std::min(xe::kMaxBlocksPerLaunch, (CORR_MAX_BLOCK_LEN) / ctx->block_len);
-  if (ctx->d_pitched) per = 1;  // one pitched staging buffer
-  per = std::max(per, 1);
+  const int per = ctx->per_launch;
   XParams p;
-  p.units = ctx->d_units;
-  p.n_tpl = ctx->n_tpl;
-  p.n_chan = ctx->n_chan;
-  p.n_in = ctx->n_in;
-  p.chunks_per_block = (ctx->block_len + xe::kChunkSamples - 1) / xe::kChunkSamples;
-  p.pk_per_block = (ctx->block_len + xe::kPkSamples - 1) / xe::kPkSamples;
-  p.n_pairs = ctx->n_pairs;
-  p.acc = ctx->d_acc;
+  std::memset(&p, 0, sizeof(p));
+  p.probs = ctx->d_prob;
   p.status = ctx->d_status;
   p.timeout_ns = ctx->timeout_ns;
   p.z_stages = ctx->z_stages;
   p.pk_stages = ctx->pk_stages;
   p.z_stage_bytes = ctx->z_stage_bytes;
   p.pk_stage_bytes = ctx->pk_stage_bytes;
-  const long long n_work = (long long)ctx->n_tpl * ctx->n_chan;
-  const int grid = (int)std::min<long long>(n_work, ctx->n_sm);
   int rc;
   for (int k0 = 0; k0 < n_blocks; k0 += per) {
     const int nb = std::min(per, n_blocks - k0);
@@ -349,8 +258,11 @@ int corr_push_blocks(corr_ctx *ctx, const uint8_t *const *d_blocks, int n_blocks
       if ((rc = encode_block_map(ctx, src, reinterpret_cast<CUtensorMap *>(maps.m[k]))) != CORR_OK)
         return rc;
     }
-    p.n_blocks = nb;
-    if ((rc = cuda_err(xe::launch_cmac(maps, p, grid, ctx->smem_bytes, st))) != CORR_OK) return rc;
+    const ItemPlan &pl = ctx->plans[nb];
+    p.items = pl.d_items;
+    p.cta_first = pl.d_cta_first;
+    if ((rc = cuda_err(xe::launch_cmac(maps, p, pl.grid, ctx->smem_bytes, st))) != CORR_OK)
+      return rc;
     ctx->launches++;
     ctx->samples += (long long)nb * ctx->block_len;
   }
@@ -459,8 +371,40 @@ int corr_check(corr_ctx *ctx, void *stream) {
 }
 
 int corr_plan(int n_in, uint8_t *cover, int *n_units, long long *issued_cmacs) {
-  if (n_in <= 0 || n_in > CORR_MAX_INPUTS) return CORR_EINVAL;
-  std::vector<XUnit> units = build_schedule(n_in);
+  return corr_plan_cover(n_in, CORR_COVER_WINDOW, cover, n_units, issued_cmacs);
+}
+
+int corr_plan_items(int n_in, int n_chan, int block_len, int n_blocks, int cover, int grid,
+                    int *items, int cap, int *n_items, int *cta_first, int *used_grid) {
+  if (n_in <= 0 || n_in > CORR_MAX_INPUTS || n_chan <= 0 || block_len <= 0 ||
+      block_len > CORR_MAX_BLOCK_LEN || n_blocks <= 0 || grid <= 0 || cover < 0 || cover > 2 ||
+      (long long)n_blocks * block_len > CORR_MAX_BLOCK_LEN)
+    return CORR_EINVAL;
+  const std::vector<XUnit> units = xe::build_schedule(n_in, cover);
+  std::vector<xe::XItem> it;
+  std::vector<int> first;
+  const int used = xe::build_items({{&units, n_chan, block_len, n_blocks}}, grid, it, first);
+  if (n_items) *n_items = (int)it.size();
+  if (used_grid) *used_grid = used;
+  if (cta_first)
+    for (int k = 0; k <= used; ++k) cta_first[k] = first[k];
+  if (items) {
+    if (cap < (int)it.size()) return CORR_EINVAL;
+    for (size_t k = 0; k < it.size(); ++k) {
+      items[5 * k + 0] = it[k].prob;
+      items[5 * k + 1] = it[k].tpl;
+      items[5 * k + 2] = it[k].chan;
+      items[5 * k + 3] = it[k].pk0;
+      items[5 * k + 4] = it[k].npk;
+    }
+  }
+  return CORR_OK;
+}
+
+int corr_plan_cover(int n_in, int cover_kind, uint8_t *cover, int *n_units,
+                    long long *issued_cmacs) {
+  if (n_in <= 0 || n_in > CORR_MAX_INPUTS || cover_kind < 0 || cover_kind > 2) return CORR_EINVAL;
+  std::vector<XUnit> units = xe::build_schedule(n_in, cover_kind);
   long long issued = 0;
   for (const XUnit &u : units) {
     for (int sg = 0; sg < u.n_seg; ++sg) {

@@ -25,11 +25,15 @@
 
 namespace {
 
-// The scratch: [status word, padded to 256 bytes][tile schedule].
+// The scratch: [status word, padded to 256 bytes][problem descriptor,
+// padded to 128 bytes][tile schedule].
 static __device__ __align__(256) unsigned char g_static_scratch[CORR_STATIC_SCRATCH_BYTES];
 
 constexpr int kStatusBytes = 256;
-constexpr int kMaxStaticUnits = (CORR_STATIC_SCRATCH_BYTES - kStatusBytes) / (int)sizeof(xe::XUnit);
+constexpr int kProbBytes = 128;
+static_assert(sizeof(xe::XProb) <= kProbBytes, "problem descriptor slot");
+constexpr int kMaxStaticUnits =
+    (CORR_STATIC_SCRATCH_BYTES - kStatusBytes - kProbBytes) / (int)sizeof(xe::XUnit);
 static_assert(kMaxStaticUnits >= 4, "scratch must hold the schedule of up to 256 inputs");
 
 constexpr int kMaxDevices = 64;
@@ -169,12 +173,26 @@ extern "C" int corr_xcorr_static(const uint8_t *d_block, int n_ant, int n_pol, i
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   unsigned char *scratch = g_scratch_addr[dev];
   int *d_status = reinterpret_cast<int *>(scratch);
-  xe::XUnit *d_units = reinterpret_cast<xe::XUnit *>(scratch + kStatusBytes);
+  xe::XProb *d_prob = reinterpret_cast<xe::XProb *>(scratch + kStatusBytes);
+  xe::XUnit *d_units = reinterpret_cast<xe::XUnit *>(scratch + kStatusBytes + kProbBytes);
   const size_t vis_bytes = (size_t)n_chan * (size_t)(N * (N + 1) / 2) * 16;
+  xe::XProb prob;
+  std::memset(&prob, 0, sizeof(prob));
+  prob.units = d_units;
+  prob.acc = d_vis;
+  prob.n_pairs = N * (N + 1) / 2;
+  prob.n_in = (int)N;
+  prob.chunks_per_block = (block_len + xe::kChunkSamples - 1) / xe::kChunkSamples;
+  prob.pk_per_block = (block_len + xe::kPkSamples - 1) / xe::kPkSamples;
+  prob.map0 = 0;
   // the scratch keeps the previous call's contents: rewrite the schedule and
-  // clear the status word; the visibilities accumulate from zero
+  // the problem, and clear the status word; the visibilities accumulate from
+  // zero.  The host copies are pageable, so each returns once its bytes are
+  // staged and the locals may go out of scope.
   if ((rc = rc_of(cudaMemcpyAsync(d_units, units, n_tpl * sizeof(xe::XUnit), cudaMemcpyHostToDevice,
                                   st))) != CORR_OK ||
+      (rc = rc_of(cudaMemcpyAsync(d_prob, &prob, sizeof(prob), cudaMemcpyHostToDevice, st))) !=
+          CORR_OK ||
       (rc = rc_of(cudaMemsetAsync(d_status, 0, sizeof(int), st))) != CORR_OK ||
       (rc = rc_of(cudaMemsetAsync(d_vis, 0, vis_bytes, st))) != CORR_OK ||
       (rc = rc_of(xe::cmac_set_smem(optin))) != CORR_OK)
@@ -193,15 +211,13 @@ extern "C" int corr_xcorr_static(const uint8_t *d_block, int n_ant, int n_pol, i
     return CORR_ECUDA;
 
   xe::XParams p;
-  p.units = d_units;
-  p.n_tpl = n_tpl;
-  p.n_chan = n_chan;
-  p.n_in = (int)N;
-  p.chunks_per_block = (block_len + xe::kChunkSamples - 1) / xe::kChunkSamples;
-  p.pk_per_block = (block_len + xe::kPkSamples - 1) / xe::kPkSamples;
-  p.n_blocks = 1;
-  p.n_pairs = N * (N + 1) / 2;
-  p.acc = d_vis;
+  std::memset(&p, 0, sizeof(p));
+  p.probs = d_prob;
+  p.items = nullptr;  // whole units, dealt round-robin over the CTAs
+  p.cta_first = nullptr;
+  p.implicit_n_tpl = n_tpl;
+  p.implicit_n_chan = n_chan;
+  p.implicit_npk = prob.pk_per_block;
   p.status = d_status;
   p.timeout_ns = 2000000000ull;
   p.z_stages = z_stages;

@@ -1,0 +1,301 @@
+// sched.cu -- triangle covers, shared-memory stage layout and the balanced
+// split of a launch into per-CTA item runs (host code only).
+#include "sched.h"
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+namespace xe {
+
+namespace {
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+void add_seg(XUnit &u, int a_zrow, int b_zrow, int b_sbo, int n, int row_in0, int col_in0) {
+  XSeg &s = u.seg[u.n_seg];
+  int col = 0;
+  for (int k = 0; k < u.n_seg; ++k) col += u.seg[k].n;
+  s.a_zrow = a_zrow;
+  s.b_zrow = b_zrow;
+  s.b_sbo = b_sbo;
+  s.n = n;
+  s.tmem_col = col;
+  s.row_in0 = row_in0;
+  s.col_in0 = col_in0;
+  u.n_seg++;
+  u.work += n;
+}
+
+void add_reg(XUnit &u, int in_lo, int n_in, int interleaved) {
+  XRegion &r = u.reg[u.n_reg];
+  r.in_lo = in_lo;
+  r.n_in = n_in;
+  r.interleaved = interleaved;
+  r.z_row = u.z_rows;
+  r.pk_off = u.pk_bytes;
+  u.z_rows += interleaved ? 2 * n_in : n_in;
+  u.pk_bytes += n_in * kPackedRowBytes;
+  u.n_reg++;
+}
+
+XUnit empty_unit() {
+  XUnit u;
+  std::memset(&u, 0, sizeof(u));
+  return u;
+}
+
+}  // namespace
+
+// Tiles of 64 inputs (rows) cover the lower triangle strip by strip: row tile
+// t needs columns [0, min(64 (t + 1), N)).  Within a unit, columns are staged
+// once per chunk and shared by all its row tiles.
+std::vector<XUnit> build_schedule(int N, int cover) {
+  std::vector<XUnit> units;
+  const int n16 = round_up(N, 16);
+  const int n_rt = (N + kTileInputs - 1) / kTileInputs;
+  if (N <= 256 && cover == kCoverWindow) {
+    std::vector<int> tiles(n_rt);
+    for (int t = 0; t < n_rt; ++t) tiles[t] = n_rt - 1 - t;  // largest strip first
+    std::vector<std::vector<int>> bins;
+    std::vector<int> used;
+    for (int t : tiles) {
+      const int n = std::min(kTileInputs * (t + 1), n16);
+      bool placed = false;
+      for (size_t k = 0; k < bins.size(); ++k)
+        if (used[k] + n <= kTmemCols) {
+          bins[k].push_back(t);
+          used[k] += n;
+          placed = true;
+          break;
+        }
+      if (!placed) {
+        bins.push_back({t});
+        used.push_back(n);
+      }
+    }
+    for (auto &bin : bins) {
+      XUnit u = empty_unit();
+      int t_max = 0;
+      for (int t : bin) t_max = std::max(t_max, t);
+      add_reg(u, 0, kTileInputs * (t_max + 1), 1);
+      for (int t : bin)
+        add_seg(u, 128 * t, 0, 2048, std::min(kTileInputs * (t + 1), n16), kTileInputs * t, 0);
+      units.push_back(u);
+    }
+  } else if (N <= 256 && cover == kCoverStrips) {
+    for (int t = n_rt - 1; t >= 0; --t) {
+      XUnit u = empty_unit();
+      add_reg(u, 0, kTileInputs * (t + 1), 1);
+      add_seg(u, 128 * t, 0, 2048, std::min(kTileInputs * (t + 1), n16), kTileInputs * t, 0);
+      units.push_back(u);
+    }
+  } else {
+    // pairs of row tiles (2m, 2m+1) against 256-column pieces of their strip
+    for (int m = 0; 2 * m < n_rt; ++m) {
+      const int t0 = 2 * m;
+      const bool two = t0 + 1 < n_rt;
+      const int row_lo = kTileInputs * t0;
+      const int kd = row_lo / 256;  // piece holding the diagonal
+      for (int k = 0; k <= kd; ++k) {
+        XUnit u = empty_unit();
+        if (k < kd) {
+          add_reg(u, row_lo, two ? 128 : 64, 1);
+          add_reg(u, 256 * k, 256, 0);
+          const int bz = u.reg[1].z_row;
+          add_seg(u, 0, bz, 1024, 256, row_lo, 256 * k);
+          if (two) add_seg(u, 128, bz, 1024, 256, row_lo + 64, 256 * k);
+        } else {
+          const int lo = 256 * k;
+          const int hi = row_lo + (two ? 128 : 64);
+          add_reg(u, lo, hi - lo, 1);
+          const int a0 = 2 * (row_lo - lo);
+          add_seg(u, a0, 0, 2048, std::min(row_lo + 64, n16) - lo, row_lo, lo);
+          if (two) add_seg(u, a0 + 128, 0, 2048, std::min(row_lo + 128, n16) - lo, row_lo + 64, lo);
+        }
+        units.push_back(u);
+      }
+    }
+  }
+  std::stable_sort(units.begin(), units.end(),
+                   [](const XUnit &a, const XUnit &b) { return a.work > b.work; });
+  return units;
+}
+
+bool stage_layout(const std::vector<const std::vector<XUnit> *> &unit_sets, int smem_optin,
+                  int max_z, StageLayout *out) {
+  int max_zr = 0, max_pk = 0;
+  for (const auto *set : unit_sets)
+    for (const XUnit &u : *set) {
+      max_zr = std::max(max_zr, u.z_rows);
+      max_pk = std::max(max_pk, u.pk_bytes);
+    }
+  StageLayout L;
+  L.z_stage_bytes = (uint32_t)round_up(max_zr * 128, 1024);
+  L.pk_stage_bytes = (uint32_t)round_up(max_pk, 1024);  // swizzled TMA destination
+  const int fixed = 1024 /* alignment slack */ + 256 /* barriers, TMEM address, flags */;
+  static_assert(8 * (2 * 4 + 2 * 4 + 2 + kMmaWarps) + 8 <= 256, "barrier area");
+  // three packed stages (bytes in flight for HBM) if that leaves two or more
+  // operand stages, else two
+  int zs = 0;
+  for (int ps = 3; ps >= 2 && zs < 2; --ps) {
+    L.pk_stages = ps;
+    zs = (smem_optin - fixed - ps * (int)L.pk_stage_bytes) / (int)L.z_stage_bytes;
+  }
+  zs = std::min(zs, std::min(max_z, 4));
+  if (zs < 2) return false;
+  L.z_stages = zs;
+  L.smem_bytes = fixed + zs * (int)L.z_stage_bytes + L.pk_stages * (int)L.pk_stage_bytes;
+  // one CTA per SM: the kernel holds all 512 TMEM columns
+  L.smem_bytes = std::max(L.smem_bytes, smem_optin / 2 + 1024);
+  L.smem_bytes = std::min(L.smem_bytes, smem_optin);
+  *out = L;
+  return true;
+}
+
+int build_items(const std::vector<ProbWork> &probs, int grid, std::vector<XItem> &items,
+                std::vector<int> &cta_first, int min_split_pk) {
+  items.clear();
+  cta_first.clear();
+  // Cost model, in operand-row chunks: unpacking one 64-sample chunk of one
+  // operand row costs 1; the fold of a unit costs kFold per accumulator
+  // column (its int64 atomic adds and the TMEM drain).
+  constexpr long long kFold = 16;
+  struct PW {
+    int cpb, ppb, npk;
+  };
+  std::vector<PW> pw(probs.size());
+  long long total = 0;
+  for (size_t p = 0; p < probs.size(); ++p) {
+    const ProbWork &pr = probs[p];
+    pw[p].cpb = (pr.block_len + kChunkSamples - 1) / kChunkSamples;
+    pw[p].ppb = (pr.block_len + kPkSamples - 1) / kPkSamples;
+    pw[p].npk = pw[p].ppb * pr.n_blocks;
+    for (const XUnit &u : *pr.units)
+      total += (long long)pr.n_chan *
+               ((long long)pw[p].cpb * pr.n_blocks * u.z_rows + kFold * u.work);
+  }
+  if (total == 0 || grid <= 0) {
+    cta_first.push_back(0);
+    return 0;
+  }
+  // cost of stages [a, b) of a unit with z_rows rows
+  auto range_cost = [&](size_t p, int a, int b, int z_rows) {
+    long long chunks = 0;
+    for (int k = a; k < b; ++k) {
+      const int kc = k % pw[p].ppb;
+      chunks += std::min(kChunksPerPk, pw[p].cpb - kChunksPerPk * kc);
+    }
+    return chunks * z_rows;
+  };
+  long long remaining = total, load = 0;
+  int cta = 0;
+  long long target = (remaining + grid - 1) / grid;
+  cta_first.push_back(0);
+  auto close_cta = [&]() {
+    remaining -= load;
+    load = 0;
+    ++cta;
+    cta_first.push_back((int)items.size());
+    if (cta < grid) target = (remaining + (grid - cta) - 1) / (grid - cta);
+  };
+  for (size_t p = 0; p < probs.size(); ++p) {
+    const ProbWork &pr = probs[p];
+    for (int t = 0; t < (int)pr.units->size(); ++t) {
+      const XUnit &u = (*pr.units)[t];
+      const long long fold = kFold * u.work;
+      for (int c = 0; c < pr.n_chan; ++c) {
+        int pk = 0;
+        const int npk = pw[p].npk;
+        while (pk < npk) {
+          if (cta == grid - 1) {  // the last CTA takes everything left
+            const long long cost = range_cost(p, pk, npk, u.z_rows) + fold;
+            items.push_back({(int)p, t, c, pk, npk - pk});
+            load += cost;
+            pk = npk;
+            continue;
+          }
+          const long long rest = range_cost(p, pk, npk, u.z_rows) + fold;
+          if (load + rest <= target) {
+            items.push_back({(int)p, t, c, pk, npk - pk});
+            load += rest;
+            pk = npk;
+            if (load >= target) close_cta();
+            continue;
+          }
+          // the rest overflows this CTA: take the stages that fit, if that
+          // leaves pieces of at least min_split_pk stages on both sides
+          int n = 0;
+          const long long room = target - load - fold;
+          if (room > 0) {
+            const long long per = (long long)kChunksPerPk * u.z_rows;
+            n = (int)std::min<long long>(npk - pk, room / per);
+            while (n > 0 && range_cost(p, pk, pk + n, u.z_rows) > room) --n;
+          }
+          if (n >= min_split_pk && npk - pk - n >= min_split_pk) {
+            items.push_back({(int)p, t, c, pk, n});
+            load += range_cost(p, pk, pk + n, u.z_rows) + fold;
+            remaining += fold;  // the rest of the unit is folded once more
+            pk += n;
+            close_cta();
+          } else if (load == 0 || 2 * (load + rest - target) < rest) {
+            // no useful split: the whole rest goes here when this CTA is
+            // empty or when most of the rest fits
+            items.push_back({(int)p, t, c, pk, npk - pk});
+            load += rest;
+            pk = npk;
+            close_cta();
+          } else {
+            close_cta();
+          }
+        }
+      }
+    }
+  }
+  if (load > 0 || (int)cta_first.size() == 1) close_cta();
+  // drop trailing empty CTAs
+  while (cta_first.size() > 2 && cta_first[cta_first.size() - 2] == cta_first.back())
+    cta_first.pop_back();
+  return (int)cta_first.size() - 1;
+}
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+bool encode_block_map(const void *base, int block_len, int n_in, int n_chan, int pitch, void *map) {
+  static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  EncodeTiledFn enc = get_encode_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)block_len, (cuuint64_t)n_in, (cuuint64_t)n_chan};
+  const cuuint64_t strides[2] = {(cuuint64_t)pitch, (cuuint64_t)pitch * (cuuint64_t)n_in};
+  const cuuint32_t box[3] = {(cuuint32_t)kPkSamples, (cuuint32_t)kTileInputs, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_UINT8, 3,
+                   const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace xe

@@ -65,30 +65,58 @@ struct XUnit {
   XSeg seg[kMaxSegs];
 };
 
-struct XParams {
-  const XUnit *units;  // [n_tpl], heaviest first
-  int n_tpl;
-  int n_chan;
+// One correlator problem of a launch: its inputs, schedule and integration
+// buffer.  A launch may carry several independent problems (a batch).
+struct XProb {
+  const XUnit *units;    // [n_tpl] templates
+  int64_t *acc;          // [n_chan][n_pairs][2]
+  long long n_pairs;     // N(N+1)/2
   int n_in;
   int chunks_per_block;  // ceil(block_len / kChunkSamples)
   int pk_per_block;      // ceil(block_len / kPkSamples)
-  int n_blocks;          // blocks in this launch (<= kMaxBlocksPerLaunch)
-  long long n_pairs;   // N(N+1)/2
-  int64_t *acc;        // [n_chan][n_pairs][2]
-  int *status;         // device status word (bit 0: a wait timed out)
+  int map0;              // the problem's first block map in the launch's map table
+};
+
+// One piece of work: template `tpl` of problem `prob` on channel `chan`,
+// over packed stages [pk0, pk0 + npk) of the launch's blocks (stage k is
+// stage k % pk_per_block of block k / pk_per_block).  A unit (problem,
+// template, channel) may be split over several items, each folded on its
+// own: the int64 fold is an atomic add, so the pieces sum exactly.
+struct XItem {
+  int prob, tpl, chan, pk0, npk;
+};
+
+struct XParams {
+  const XProb *probs;
+  // Explicit items: CTA b runs items [cta_first[b], cta_first[b + 1]).
+  // With items == nullptr the launch holds problem 0 alone and CTA b runs the
+  // whole units b, b + grid, ... of its n_tpl x n_chan units (unit w is
+  // template w / n_chan on channel w % n_chan) over all npk stages.
+  const XItem *items;
+  const int *cta_first;
+  int implicit_n_tpl, implicit_n_chan, implicit_npk;
+  int *status;           // device status word (bit 0: a wait timed out)
   unsigned long long timeout_ns;
   int z_stages, pk_stages;
   uint32_t z_stage_bytes, pk_stage_bytes;
 };
 
-// One TMA descriptor (CUtensorMap, 128 bytes) per block of the launch.
-struct XMaps {
-  alignas(64) unsigned char m[kMaxBlocksPerLaunch][128];
+// TMA descriptors (CUtensorMap, 128 bytes each), one per (problem, block) of
+// the launch, passed as a kernel parameter.
+constexpr int kMaxMaps = 8;        // one problem, up to kMaxBlocksPerLaunch blocks
+constexpr int kMaxBatchMaps = 128; // a batch: one block per problem
+template <int M>
+struct XMapsT {
+  alignas(64) unsigned char m[M][128];
 };
+using XMaps = XMapsT<kMaxMaps>;
+using XBatchMaps = XMapsT<kMaxBatchMaps>;
 
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_cmac(const XMaps &maps, const XParams &p, int grid, int smem_bytes,
                         cudaStream_t stream);
+cudaError_t launch_cmac_batch(const XBatchMaps &maps, const XParams &p, int grid, int smem_bytes,
+                              cudaStream_t stream);
 cudaError_t cmac_set_smem(int smem_bytes);
 cudaError_t launch_dump(int64_t *acc, int64_t *vis, int64_t *stokes, int n_ant, int n_pol,
                         int n_chan, cudaStream_t stream, int grid);

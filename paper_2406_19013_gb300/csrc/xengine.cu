@@ -27,10 +27,14 @@
 //               re/im between lanes, int64 red.add into the lower triangle
 // A launch integrates up to kMaxBlocksPerLaunch blocks before the fold, as
 // long as the samples per fold keep every fp32 partial below 2^24.
-// A work unit is (channel, template); a template names the inputs staged
-// per chunk and the MMAs (row tile x column range) that cover its part of
-// the triangle.  All waits are bounded by a timeout; on expiry the kernel
-// drains its own copies and MMAs, frees TMEM and reports through *status.
+// A work unit is (problem, template, channel); a template names the inputs
+// staged per chunk and the MMAs (row tile x column range) that cover its part
+// of the triangle.  The host cuts the units into items (a unit over a range
+// of 128-sample stages) and gives every CTA a contiguous run of items of
+// about equal cost, so the last wave does not leave SMs idle; a launch may
+// hold several independent problems (a batch of correlators).  All waits are
+// bounded by a timeout; on expiry the kernel drains its own copies and MMAs,
+// frees TMEM and reports through *status.
 #include <cuda.h>
 
 #include "ptx.cuh"
@@ -88,9 +92,28 @@ __device__ __forceinline__ void red_add_s64(int64_t *addr, long long v) {
 
 }  // namespace
 
+// Item `it` of the launch (explicit list, or derived from the unit index).
+__device__ __forceinline__ XItem item_at(const XParams &p, int it) {
+  if (p.items) return p.items[it];
+  XItem r;
+  r.prob = 0;
+  r.tpl = it / p.implicit_n_chan;
+  r.chan = it - r.tpl * p.implicit_n_chan;
+  r.pk0 = 0;
+  r.npk = p.implicit_npk;
+  return r;
+}
+
+// Chunks (of kChunkSamples) in packed stage kc of a block.
+__device__ __forceinline__ int chunks_in_pk(const XProb &pb, int kc) {
+  return min(kChunksPerPk, pb.chunks_per_block - kChunksPerPk * kc);
+}
+
 // kThreads = 32 * 25: warps 0-15 unpack, 16-19 epilogue, 20 TMA, 21-24 MMA.
+// Every role walks the same item list, [cta_first[b], cta_first[b + 1]).
+template <int M>
 __global__ void __launch_bounds__(kThreads, 1)
-    xengine_cmac_kernel(const __grid_constant__ XMaps maps, const XParams p) {
+    xengine_cmac_kernel(const __grid_constant__ XMapsT<M> maps, const XParams p) {
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte alignment for the swizzled operand atoms
   uint8_t *smem = reinterpret_cast<uint8_t *>(
@@ -138,29 +161,39 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = misc[0];
 
-  const long long n_work = (long long)p.n_tpl * p.n_chan;
-  const int n_chunks = p.chunks_per_block * p.n_blocks;
+  int it0, it1, it_step;
+  if (p.items) {
+    it0 = p.cta_first[blockIdx.x];
+    it1 = p.cta_first[blockIdx.x + 1];
+    it_step = 1;
+  } else {
+    it0 = blockIdx.x;
+    it1 = p.implicit_n_tpl * p.implicit_n_chan;
+    it_step = gridDim.x;
+  }
   const uint64_t to = p.timeout_ns;
 
   if (warp == kWarpTma) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      for (int k = 0; k < p.n_blocks; ++k) prefetch_tmap(&maps.m[k][0]);
       int s = 0;
       uint32_t ph = 0;
       int armed[8];
       uint32_t armed_ph[8];
       for (int k = 0; k < 8; ++k) armed[k] = 0, armed_ph[k] = 0;
       bool ok = true;
-      for (long long w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
-        const int tpl = (int)(w / p.n_chan), c = (int)(w % p.n_chan);
-        const XUnit *u = p.units + tpl;
+      int last_map = -1;
+      for (int it = it0; it < it1 && ok; it += it_step) {
+        const XItem item = item_at(p, it);
+        const XProb pb = p.probs[item.prob];
+        const XUnit *u = pb.units + item.tpl;
         const int n_reg = u->n_reg;
         const uint32_t bytes = (uint32_t)u->pk_bytes;
-        const int n_pk = p.pk_per_block * p.n_blocks;
-        for (int k = 0; k < n_pk; ++k) {
-          const int blk = k / p.pk_per_block, kc = k - blk * p.pk_per_block;
-          const void *tmap = &maps.m[blk][0];
+        for (int k = item.pk0; k < item.pk0 + item.npk; ++k) {
+          const int blk = k / pb.pk_per_block, kc = k - blk * pb.pk_per_block;
+          const int mi = pb.map0 + blk;
+          const void *tmap = &maps.m[mi][0];
+          if (mi != last_map) { prefetch_tmap(tmap); last_map = mi; }
           if (!mbar_wait(b.pk_empty + 8 * s, ph ^ 1u, abort_flag, to)) { ok = false; break; }
           const uint32_t full = b.pk_full + 8 * s;
           mbar_arrive_expect_tx(full, bytes);
@@ -171,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int in_lo = u->reg[r].in_lo, n_in = u->reg[r].n_in, off = u->reg[r].pk_off;
             for (int bx = 0; bx < n_in; bx += kTileInputs)
               tma_load_3d(dst0 + off + bx * kPackedRowBytes, tmap, full, kc * kPkSamples,
-                          in_lo + bx, c);
+                          in_lo + bx, item.chan);
           }
           if (++s == p.pk_stages) { s = 0; ph ^= 1u; }
         }
@@ -192,8 +225,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t zph = 0;
       long long nu = 0;
       bool ok = true;
-      for (long long w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++nu) {
-        const XUnit *u = p.units + (int)(w / p.n_chan);
+      for (int it = it0; it < it1 && ok; it += it_step, ++nu) {
+        const XItem item = item_at(p, it);
+        const XProb pb = p.probs[item.prob];
+        const XUnit *u = pb.units + item.tpl;
         const int n_seg = u->n_seg;
         static_assert(kMaxSegs / kMmaWarps == 2, "two segments per issuer at most");
         // the (at most two) segments this issuer owns, held in registers
@@ -201,26 +236,31 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int n_mine = (m < n_seg) + (m + kMmaWarps < n_seg);
         if (nu > 0 && !mbar_wait(b.acc_empty, (uint32_t)((nu - 1) & 1), abort_flag, to)) break;
         tc_fence_after();
-        for (int k = 0; k < n_chunks; ++k) {
-          if (!mbar_wait(b.z_full + 8 * zs, zph, abort_flag, to)) { ok = false; break; }
-          tc_fence_after();
-          const uint32_t zb = smem_u32(z_buf + (size_t)zs * p.z_stage_bytes);
+        bool first = true;  // the item's first chunk overwrites the accumulators
+        for (int k = item.pk0; k < item.pk0 + item.npk && ok; ++k) {
+          const int nch = chunks_in_pk(pb, k % pb.pk_per_block);
+          for (int sub = 0; sub < nch; ++sub) {
+            if (!mbar_wait(b.z_full + 8 * zs, zph, abort_flag, to)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t zb = smem_u32(z_buf + (size_t)zs * p.z_stage_bytes);
 #pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            if (j >= n_mine) break;
-            const XSeg &sgm = j == 0 ? mine0 : mine1;
-            const uint32_t idesc = idesc_e5m2_f32(128, sgm.n);
-            const uint32_t a0 = zb + (uint32_t)sgm.a_zrow * 128u;
-            const uint32_t b0 = zb + (uint32_t)sgm.b_zrow * 128u;
+            for (int j = 0; j < 2; ++j) {
+              if (j >= n_mine) break;
+              const XSeg &sgm = j == 0 ? mine0 : mine1;
+              const uint32_t idesc = idesc_e5m2_f32(128, sgm.n);
+              const uint32_t a0 = zb + (uint32_t)sgm.a_zrow * 128u;
+              const uint32_t b0 = zb + (uint32_t)sgm.b_zrow * 128u;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t da = sdesc_sw128(a0 + 32u * kk, 1024u);
-              const uint64_t db = sdesc_sw128(b0 + 32u * kk, (uint32_t)sgm.b_sbo);
-              mma_f8_ss(tmem + (uint32_t)sgm.tmem_col, da, db, idesc, (k | kk) != 0);
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t da = sdesc_sw128(a0 + 32u * kk, 1024u);
+                const uint64_t db = sdesc_sw128(b0 + 32u * kk, (uint32_t)sgm.b_sbo);
+                mma_f8_ss(tmem + (uint32_t)sgm.tmem_col, da, db, idesc, !(first && kk == 0));
+              }
             }
+            first = false;
+            mma_commit(b.z_empty + 8 * zs);
+            if (++zs == p.z_stages) { zs = 0; zph ^= 1u; }
           }
-          mma_commit(b.z_empty + 8 * zs);
-          if (++zs == p.z_stages) { zs = 0; zph ^= 1u; }
         }
         if (ok) mma_commit(b.acc_full);
       }
@@ -231,23 +271,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp < kUnpackWarps) {
     // ------------------------------------------------------------ unpack
-    // Work item = (input row, 8-sample quarter of the 32-sample chunk).
     const int tid = threadIdx.x;
-    static_assert(kUnpackWarps >= 1, "unpack threads = 8 rows x 4 sample groups per warp");
     int s = 0, zs = 0;
     uint32_t ph = 0, zph = 0;
     bool ok = true;
-    for (long long w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
-      const XUnit *u = p.units + (int)(w / p.n_chan);
+    for (int it = it0; it < it1 && ok; it += it_step) {
+      const XItem item = item_at(p, it);
+      const XProb pb = p.probs[item.prob];
+      const XUnit *u = pb.units + item.tpl;
       const int n_reg = u->n_reg;
       // the (at most two) staged regions, held in registers
       const XRegion rg0 = u->reg[0], rg1 = u->reg[n_reg > 1 ? 1 : 0];
-      for (int blk = 0; blk < p.n_blocks && ok; ++blk) {
-        for (int kb = 0; kb < p.chunks_per_block; ++kb) {
-          const int sub = kb % kChunksPerPk;  // operand chunk within the packed stage
-          if (sub == 0 && !mbar_wait(b.pk_full + 8 * s, ph, abort_flag, to)) { ok = false; break; }
+      for (int k = item.pk0; k < item.pk0 + item.npk && ok; ++k) {
+        const int nch = chunks_in_pk(pb, k % pb.pk_per_block);
+        if (!mbar_wait(b.pk_full + 8 * s, ph, abort_flag, to)) { ok = false; break; }
+        const uint8_t *pk = pk_buf + (size_t)s * p.pk_stage_bytes;
+        for (int sub = 0; sub < nch; ++sub) {
           if (!mbar_wait(b.z_empty + 8 * zs, zph ^ 1u, abort_flag, to)) { ok = false; break; }
-          const uint8_t *pk = pk_buf + (size_t)s * p.pk_stage_bytes;
           uint8_t *zst = z_buf + (size_t)zs * p.z_stage_bytes;
           // operand chunk `sub` of the packed stage (64 of its 128 samples)
 #pragma unroll
@@ -268,14 +308,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int dst_step = (rg.interleaved ? 2 * R : R) * 128;  // R rows further on
             const int n_k = row0 < rg.n_in ? (rg.n_in - row0 + R - 1) / R : 0;
 #pragma unroll 2
-            for (int k = 0; k < n_k; ++k) {
-              const uint4 in = *reinterpret_cast<const uint4 *>(src + k * R * kPackedRowBytes);
+            for (int kr = 0; kr < n_k; ++kr) {
+              const uint4 in = *reinterpret_cast<const uint4 *>(src + kr * R * kPackedRowBytes);
               uint2 a0, q0, a1, q1, a2, q2, a3, q3;
               decode_word(in.x, a0, q0);
               decode_word(in.y, a1, q1);
               decode_word(in.z, a2, q2);
               decode_word(in.w, a3, q3);
-              uint8_t *d = dst + k * dst_step;
+              uint8_t *d = dst + kr * dst_step;
               *reinterpret_cast<uint4 *>(d + off0) = make_uint4(a0.x, a0.y, a1.x, a1.y);
               *reinterpret_cast<uint4 *>(d + off1) = make_uint4(a2.x, a2.y, a3.x, a3.y);
               if (rg.interleaved) {
@@ -286,14 +326,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           fence_proxy_async_smem();
           __syncwarp();
-          const bool last_of_pk = sub == kChunksPerPk - 1 || kb == p.chunks_per_block - 1;
           if (lane == 0) {
             mbar_arrive(b.z_full + 8 * zs);
-            if (last_of_pk) mbar_arrive(b.pk_empty + 8 * s);
+            if (sub == nch - 1) mbar_arrive(b.pk_empty + 8 * s);
           }
-          if (last_of_pk && ++s == p.pk_stages) { s = 0; ph ^= 1u; }
           if (++zs == p.z_stages) { zs = 0; zph ^= 1u; }
         }
+        if (++s == p.pk_stages) { s = 0; ph ^= 1u; }
       }
     }
   } else if (warp < kWarpTma) {
@@ -302,17 +341,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int rho = 32 * q + lane;
     const int g = rho >> 4, is_im = (rho >> 3) & 1, l = rho & 7;
     long long nu = 0;
-    for (long long w = blockIdx.x; w < n_work; w += gridDim.x, ++nu) {
-      const int tpl = (int)(w / p.n_chan), c = (int)(w % p.n_chan);
-      const XUnit *u = p.units + tpl;
+    for (int it = it0; it < it1; it += it_step, ++nu) {
+      const XItem item = item_at(p, it);
+      const XProb pb = p.probs[item.prob];
+      const XUnit *u = pb.units + item.tpl;
+      const int c = item.chan;
       if (!mbar_wait(b.acc_full, (uint32_t)(nu & 1), abort_flag, to)) break;
       tc_fence_after();
       const int n_seg = u->n_seg;
       for (int sg = 0; sg < n_seg; ++sg) {
         const XSeg sgm = u->seg[sg];
         const int i = sgm.row_in0 + 8 * g + l;
-        const bool row_ok = i < p.n_in;
-        int64_t *arow = p.acc + ((long long)c * p.n_pairs + (long long)i * (i + 1) / 2) * 2;
+        const bool row_ok = i < pb.n_in;
+        int64_t *arow = pb.acc + ((long long)c * pb.n_pairs + (long long)i * (i + 1) / 2) * 2;
         for (int cb = 0; cb < sgm.n; cb += 16) {
           uint32_t v[16];
           __syncwarp();
@@ -356,13 +397,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 cudaError_t cmac_set_smem(int smem_bytes) {
-  return cudaFuncSetAttribute(xengine_cmac_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem_bytes);
+  cudaError_t e = cudaFuncSetAttribute(xengine_cmac_kernel<kMaxMaps>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(xengine_cmac_kernel<kMaxBatchMaps>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
 }
 
 cudaError_t launch_cmac(const XMaps &maps, const XParams &p, int grid, int smem_bytes,
                         cudaStream_t stream) {
-  xengine_cmac_kernel<<<grid, kThreads, smem_bytes, stream>>>(maps, p);
+  xengine_cmac_kernel<kMaxMaps><<<grid, kThreads, smem_bytes, stream>>>(maps, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cmac_batch(const XBatchMaps &maps, const XParams &p, int grid, int smem_bytes,
+                              cudaStream_t stream) {
+  xengine_cmac_kernel<kMaxBatchMaps><<<grid, kThreads, smem_bytes, stream>>>(maps, p);
   return cudaGetLastError();
 }
 

@@ -185,3 +185,36 @@ def workload(name: str, seed: int = 1) -> Workload:
         return Workload(name, 1024, 2, 256, 4096, 16, seed,
                         gradient_tones(n, th, [1.2, 1.2, 1.2], [0.0, 17 / 4096, 101 / 4096]))
     raise KeyError(name)
+
+
+# Input counts of the batched workload: arrays from 16 to 256 dual-pol antennas
+BATCH_N = (32, 64, 128, 192, 256, 512)
+
+
+def batched_instances(n_inst: int = 64, seed: int = 3):
+    """Shapes of a batch of independent correlators: n_inst tuples
+    (n_ant, n_pol, n_chan, block_len).  Input counts cycle through BATCH_N
+    (dual-pol), channel counts are uniform in [16, 1024] and block lengths
+    uniform in [256, 16384] on a 16-sample grid (so rows need no re-pitching,
+    while most are not whole 64-sample chunks)."""
+    rng = np.random.default_rng([seed, 0xBA7C])
+    out = []
+    for k in range(n_inst):
+        n = BATCH_N[k % len(BATCH_N)]
+        c = int(rng.integers(16, 1025))
+        t = 16 * int(rng.integers(16, 1025))
+        out.append((n // 2, 2, c, t))
+    return out
+
+
+def pool_offsets(sizes, pool_bytes: int, seed: int = 4):
+    """Seeded 16-byte-aligned start offsets of windows of the given sizes in a
+    byte pool of pool_bytes (every window fits)."""
+    rng = np.random.default_rng([seed, 0x9001])
+    out = []
+    for sz in sizes:
+        span = pool_bytes - int(sz)
+        if span < 0:
+            raise ValueError("window larger than the pool")
+        out.append(16 * int(rng.integers(0, span // 16 + 1)))
+    return out

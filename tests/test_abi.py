@@ -89,3 +89,76 @@ def test_plan_rejects(corr):
         corr.plan(0)
     with pytest.raises(corr.CorrError):
         corr.plan(8193)
+
+
+@pytest.mark.parametrize("cover", [0, 1, 2])
+@pytest.mark.parametrize("n", [1, 16, 40, 64, 65, 127, 128, 192, 200, 256, 257, 512, 1000])
+def test_every_cover_covers_lower_triangle_once(corr, n, cover):
+    _, issued, got = corr.plan_cover(n, cover, with_cover=True)
+    assert np.array_equal(got, np.tril(np.ones((n, n), dtype=np.uint8)))
+    assert issued >= n * (n + 1) // 2
+
+
+def _check_split(corr, n_in, n_chan, block_len, n_blocks, grid, cover=0, min_split=16):
+    items, first = corr.plan_items(n_in, n_chan, block_len, n_blocks, grid, cover)
+    n_tpl = corr.plan_cover(n_in, cover)[0]
+    ppb = -(-block_len // 128)
+    npk = ppb * n_blocks
+    used = len(first) - 1
+    assert 1 <= used <= grid
+    assert first[0] == 0 and first[-1] == len(items)
+    assert np.all(np.diff(first) >= 1)  # no empty CTA
+    # every (template, channel, stage) exactly once
+    seen = np.zeros((n_tpl, n_chan, npk), dtype=np.int32)
+    for prob, tpl, chan, pk0, n in items:
+        assert prob == 0 and n >= 1 and 0 <= pk0 and pk0 + n <= npk
+        seen[tpl, chan, pk0:pk0 + n] += 1
+    assert np.all(seen == 1)
+    # a unit is split only into pieces of >= min_split stages
+    pieces = {}
+    for prob, tpl, chan, pk0, n in items:
+        pieces.setdefault((tpl, chan), []).append(n)
+    for ns in pieces.values():
+        if len(ns) > 1:
+            assert min(ns) >= min(min_split, npk)
+    return items, first
+
+
+def test_item_split_balances_the_paper_launch(corr):
+    # 192 inputs, 1024 channels, 8 blocks of 8192 samples over 152 SMs:
+    # whole units would give some SMs 7 units and others 6
+    items, first = _check_split(corr, 192, 1024, 8192, 8, 152)
+    stages = np.zeros(len(first) - 1)
+    for b in range(len(first) - 1):
+        stages[b] = items[first[b]:first[b + 1], 4].sum()
+    # stages differ only by the modelled fold cost of an extra item
+    assert stages.max() / stages.mean() < 1.02
+    # dealing whole units would leave 7 x 512 stages on the busiest SM
+    assert stages.max() < 0.98 * 7 * 512
+    assert len(first) - 1 == 152
+
+
+@pytest.mark.parametrize("args", [(16, 64, 2048, 1, 152), (192, 5, 1008, 1, 152),
+                                  (40, 3, 256, 2, 152), (512, 37, 4096, 1, 152),
+                                  (2048, 4, 4096, 2, 152), (100, 1, 100, 1, 4),
+                                  (192, 1024, 8192, 1, 152), (64, 16, 16384, 1, 7)])
+def test_item_split_covers_every_unit_stage_once(corr, args):
+    _check_split(corr, *args)
+
+
+@pytest.mark.parametrize("cover", [1, 2])
+def test_item_split_other_covers(corr, cover):
+    _check_split(corr, 192, 300, 4096, 2, 152, cover)
+
+
+def test_plan_items_rejects(corr):
+    with pytest.raises(corr.CorrError):
+        corr.plan_items(192, 10, 8192, 17, 152)  # 17 x 8192 samples exceed one fold
+    with pytest.raises(corr.CorrError):
+        corr.plan_items(192, 10, 8192, 1, 0)
+    with pytest.raises(corr.CorrError):
+        corr.plan_items(192, 10, 8192, 1, 152, cover=3)
+
+
+def test_tuned_cover_is_empty_without_a_gpu(corr):
+    assert corr.tuned_cover(192, 8192) == -1
