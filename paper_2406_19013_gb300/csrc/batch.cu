@@ -22,7 +22,7 @@
 #include <vector>
 
 #include "corr.h"
-#include "sched.h"
+#include "xe_sched.h"
 #include "xe_internal.h"
 
 namespace {
@@ -79,7 +79,7 @@ float time_cover(const std::vector<xe::XUnit> &units, int n_in, int C, int T, in
                  int smem_optin, uint8_t *d_x, int64_t *d_acc, int *d_status,
                  cudaStream_t st) {
   xe::StageLayout L;
-  if (!xe::stage_layout({&units}, smem_optin, 4, &L)) return -1.0f;
+  if (!xe::stage_layout({&units}, smem_optin, xe::kMaxZStages, &L)) return -1.0f;
   std::vector<xe::XItem> items;
   std::vector<int> first;
   const int grid = xe::build_items({{&units, C, T, 1}}, n_sm, items, first);
@@ -229,7 +229,7 @@ void free_batch(corr_batch *b) {
 int upload_group(corr_batch *b, BGroup &g) {
   std::vector<const std::vector<xe::XUnit> *> sets;
   for (auto &u : g.units) sets.push_back(&u);
-  if (!xe::stage_layout(sets, b->smem_optin, 4, &g.L)) return CORR_EINVAL;
+  if (!xe::stage_layout(sets, b->smem_optin, xe::kMaxZStages, &g.L)) return CORR_EINVAL;
   std::vector<xe::XUnit> all;
   std::vector<size_t> first_unit;
   for (auto &u : g.units) {
@@ -365,7 +365,7 @@ int corr_batch_create(int n_inst, const int *n_ant, const int *n_pol, const int 
   for (int k = 0; k < n_inst; ++k) {
     units[k] = xe::build_schedule(b->inst[k].n_in, b->inst[k].cover);
     xe::StageLayout L;
-    if (!xe::stage_layout({&units[k]}, optin, 4, &L)) {
+    if (!xe::stage_layout({&units[k]}, optin, xe::kMaxZStages, &L)) {
       free_batch(b);
       return CORR_EINVAL;
     }

@@ -11,7 +11,7 @@
 #include <vector>
 
 #include "corr.h"
-#include "sched.h"
+#include "xe_sched.h"
 #include "xe_internal.h"
 
 using xe::XParams;
@@ -152,7 +152,7 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
   std::vector<XUnit> units = xe::build_schedule(ctx->n_in);
   ctx->n_tpl = (int)units.size();
   xe::StageLayout L;
-  if (!xe::stage_layout({&units}, smem_optin, 4, &L)) {
+  if (!xe::stage_layout({&units}, smem_optin, xe::kMaxZStages, &L)) {
     free_ctx(ctx);
     return CORR_EINVAL;
   }

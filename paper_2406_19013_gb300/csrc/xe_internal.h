@@ -30,6 +30,12 @@ constexpr int kWarpEpi0 = kUnpackWarps;
 constexpr int kWarpTma = kWarpEpi0 + kEpiWarps;
 constexpr int kWarpMma0 = kWarpTma + 1;
 constexpr int kThreads = 32 * (kWarpMma0 + kMmaWarps);
+// Pipeline depth limits and the shared-memory area for the barriers (full and
+// empty barrier per stage, accumulator full/empty, one drain barrier per MMA
+// issuer) and the TMEM address / abort flag behind them.
+constexpr int kMaxPkStages = 8;
+constexpr int kMaxZStages = 6;
+constexpr int kBarrierBytes = 512;
 // Blocks integrated by one launch before the fold into int64.
 constexpr int kMaxBlocksPerLaunch = 8;
 

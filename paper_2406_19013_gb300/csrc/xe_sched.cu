@@ -1,6 +1,6 @@
-// sched.cu -- triangle covers, shared-memory stage layout and the balanced
+// xe_sched.cu -- triangle covers, shared-memory stage layout and the balanced
 // split of a launch into per-CTA item runs (host code only).
-#include "sched.h"
+#include "xe_sched.h"
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -135,19 +135,38 @@ bool stage_layout(const std::vector<const std::vector<XUnit> *> &unit_sets, int 
   StageLayout L;
   L.z_stage_bytes = (uint32_t)round_up(max_zr * 128, 1024);
   L.pk_stage_bytes = (uint32_t)round_up(max_pk, 1024);  // swizzled TMA destination
-  const int fixed = 1024 /* alignment slack */ + 256 /* barriers, TMEM address, flags */;
-  static_assert(8 * (2 * 4 + 2 * 4 + 2 + kMmaWarps) + 8 <= 256, "barrier area");
-  // three packed stages (bytes in flight for HBM) if that leaves two or more
-  // operand stages, else two
-  int zs = 0;
-  for (int ps = 3; ps >= 2 && zs < 2; --ps) {
-    L.pk_stages = ps;
-    zs = (smem_optin - fixed - ps * (int)L.pk_stage_bytes) / (int)L.z_stage_bytes;
+  const int fixed = 1024 /* alignment slack */ + kBarrierBytes;
+  static_assert(8 * (2 * kMaxPkStages + 2 * kMaxZStages + 2 + kMmaWarps) + 16 <= kBarrierBytes,
+                "barrier area");
+  const int avail = smem_optin - fixed;
+  const int zb = (int)L.z_stage_bytes, pb = (int)L.pk_stage_bytes;
+  const int zcap = std::min(max_z, kMaxZStages);
+  // Operand stages first (three if they fit beside three packed stages, else
+  // two beside two), then packed stages (bytes in flight from HBM) up to six,
+  // operand stages up to four, and both up to their caps while they fit.
+  int zs, ps;
+  if (3 * zb + 3 * pb <= avail && zcap >= 3) {
+    zs = 3;
+    ps = 3;
+  } else if (2 * zb + 3 * pb <= avail) {
+    zs = 2;
+    ps = 3;
+  } else if (2 * zb + 2 * pb <= avail) {
+    zs = 2;
+    ps = 2;
+  } else {
+    return false;
   }
-  zs = std::min(zs, std::min(max_z, 4));
-  if (zs < 2) return false;
+  auto grow = [&](int &v, int cap, int bytes) {
+    while (v < cap && zs * zb + ps * pb + bytes <= avail) ++v;
+  };
+  grow(ps, 6, pb);
+  grow(zs, std::min(4, zcap), zb);
+  grow(ps, kMaxPkStages, pb);
+  grow(zs, zcap, zb);
   L.z_stages = zs;
-  L.smem_bytes = fixed + zs * (int)L.z_stage_bytes + L.pk_stages * (int)L.pk_stage_bytes;
+  L.pk_stages = ps;
+  L.smem_bytes = fixed + zs * zb + ps * pb;
   // one CTA per SM: the kernel holds all 512 TMEM columns
   L.smem_bytes = std::max(L.smem_bytes, smem_optin / 2 + 1024);
   L.smem_bytes = std::min(L.smem_bytes, smem_optin);

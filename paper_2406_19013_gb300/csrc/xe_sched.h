@@ -1,4 +1,4 @@
-// sched.h -- host-side scheduling of the CMAC kernel: the cover of the lower
+// xe_sched.h -- host-side scheduling of the CMAC kernel: the cover of the lower
 // triangle by MMA tiles (templates) and the split of a launch's work into
 // per-CTA runs of items of about equal cost.  Not part of the public ABI.
 #pragma once

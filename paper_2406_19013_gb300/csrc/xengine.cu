@@ -178,9 +178,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int s = 0;
       uint32_t ph = 0;
-      int armed[8];
-      uint32_t armed_ph[8];
-      for (int k = 0; k < 8; ++k) armed[k] = 0, armed_ph[k] = 0;
+      int armed[kMaxPkStages];
+      uint32_t armed_ph[kMaxPkStages];
+      for (int k = 0; k < kMaxPkStages; ++k) armed[k] = 0, armed_ph[k] = 0;
       bool ok = true;
       int last_map = -1;
       for (int it = it0; it < it1 && ok; it += it_step) {
