@@ -462,6 +462,75 @@ def run_batched(args):
     return 0
 
 
+def run_corner_turn(args):
+    """The corner turn of the 192-input block (1.61 GB, F-engine order
+    [time][chan][input] -> [chan][input][time]) against the HBM roofline, and
+    pushes of F-engine-order blocks against pushes of turned ones."""
+    import torch
+
+    from paper_2406_19013_gb300 import Correlator, build
+    from paper_2406_19013_gb300.corr import corner_turn
+    from synth import synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    w = synth.workload("paper", seed=1)
+    hb = torch.empty((N_CHAN, N_IN, BLOCK_LEN), dtype=torch.uint8, pin_memory=True)
+    w.block(0, out=hb.numpy())
+    x = hb.to(dev)
+    x_tcn = x.permute(2, 0, 1).contiguous()  # input preparation, not timed
+    out = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, n):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    k = max(1, args.steps)
+    ms_turn = timed(lambda: corner_turn(x_tcn, out, stream), 4 * k)
+    assert torch.equal(out, x)
+    nbytes = x.numel()
+    gbs = 2 * nbytes / (ms_turn / 1e3) / 1e9
+    xc = Correlator(N_ANT, N_POL, N_CHAN, BLOCK_LEN)
+    ms_tcn = timed(lambda: xc.push_block_tcn(x_tcn, stream), k)
+    ms_plain = timed(lambda: xc.push_block(x, stream), k)
+    xc.check()
+    xc.close()
+    hbm = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm = float(json.load(f)["hbm_gbs"])
+        hbm_kind = "measured"
+    except Exception:
+        hbm, hbm_kind = 6800.0, "fallback"
+    line = {
+        "metric": "corner turn GB/s (read + write) of one 192-input block", "value": gbs,
+        "unit": "GB/s", "n_gpus": 1, "steps": 4 * k, "warmup": args.warmup,
+        "ms_per_step": ms_turn, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "uint8 [8192][1024][192] (F-engine order) -> [1024][192][8192]",
+                   "bytes_per_step": nbytes, "l2": "inputs larger than L2 (1.61 GB)"},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                     "frac": gbs / hbm, "peak_source": f"{hbm_kind} copy bandwidth",
+                     "kernel": "corner_turn_kernel"},
+        "push_f_engine_order": {"ms_per_block": ms_tcn,
+                                "tcmac_s": CMAC_PER_BLOCK / (ms_tcn / 1e3) / 1e12},
+        "push_x_engine_order": {"ms_per_block": ms_plain,
+                                "tcmac_s": CMAC_PER_BLOCK / (ms_plain / 1e3) / 1e12},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -472,9 +541,10 @@ def main():
     ap.add_argument("--group", type=int, default=8, help="blocks per corr_push_blocks call")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-channels", type=int, default=16)
-    ap.add_argument("--workload", choices=["paper", "batched"], default="paper",
+    ap.add_argument("--workload", choices=["paper", "batched", "corner_turn"], default="paper",
                     help="paper: the 192-input integration (default); batched: 64 mixed "
-                         "correlators in shared launches")
+                         "correlators in shared launches; corner_turn: the device reorder "
+                         "of F-engine-order blocks")
     ap.add_argument("--n-chan", type=int, default=N_CHAN,
                     help="channels per GPU (profiling a smaller band; the reported workload is 1024)")
     args = ap.parse_args()
@@ -487,6 +557,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "corner_turn":
+        return run_corner_turn(args)
     return run_ours(args)
 
 

@@ -226,6 +226,31 @@ int corr_plan_items(int n_in, int n_chan, int block_len, int n_blocks, int cover
 int corr_xcorr_static(const uint8_t *d_block, int n_ant, int n_pol, int n_chan, int block_len,
                       int64_t *d_vis, void *stream);
 
+/*
+ * Corner turn (Sec. 2.1: the Transpose module that reorders the F-engine
+ * output for the correlation), on the device:
+ *     d_dst[c][i][t] = d_src[t][c][i]
+ * for a block in F-engine order, uint8 [block_len][n_chan][n_in] (one
+ * spectrum per time step), to the X-engine order of corr_push_block, uint8
+ * [n_chan][n_in][block_len].  The call reads and writes every byte once.
+ *   - Any sizes are accepted.
+ *   - d_src and d_dst must be 4-byte aligned, must not overlap, and are
+ *     owned by the caller.
+ * Stream-ordered and asynchronous.  Errors: CORR_EINVAL (NULL or misaligned
+ * pointer, non-positive size), CORR_ECUDA.
+ */
+int corr_corner_turn(const uint8_t *d_src, uint8_t *d_dst, int n_in, int n_chan, int block_len,
+                     void *stream);
+
+/*
+ * As corr_push_block for a block in F-engine order, uint8
+ * [block_len][n_chan][N] (d_src, 4-byte aligned).  The block is corner-turned
+ * into a context-owned buffer, which is allocated on the first call and freed
+ * by corr_destroy, and then integrated.  d_src may be reused once the stream
+ * has executed the call.  Errors: as corr_push_block, plus CORR_ENOMEM.
+ */
+int corr_push_block_tcn(corr_ctx *ctx, const uint8_t *d_src, void *stream);
+
 /* Number of kernel launches the context has enqueued (pushes and dumps). */
 long long corr_launch_count(const corr_ctx *ctx);
 

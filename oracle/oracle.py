@@ -118,3 +118,16 @@ def pair_index(i: int, j: int) -> int:
     """Row-major lower-triangle index of (i, j), i >= j (Eq. 1's N(N+1)/2 count)."""
     assert i >= j >= 0
     return i * (i + 1) // 2 + j
+
+
+def corner_turn(x_tcn: np.ndarray) -> np.ndarray:
+    """The Transpose step of Sec. 2.1: uint8[T][C][N] (one spectrum per time
+    step) to uint8[C][N][T] (each input's samples contiguous per channel),
+    out[c][i][t] = x[t][c][i]."""
+    x = np.asarray(x_tcn)
+    assert x.dtype == np.uint8 and x.ndim == 3
+    T, C, N = x.shape
+    out = np.empty((C, N, T), dtype=np.uint8)
+    for t in range(T):
+        out[:, :, t] = x[t]
+    return out

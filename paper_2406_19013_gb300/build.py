@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcorr.so")
-SOURCES = ["xengine.cu", "dump.cu", "corr.cu", "corr_static.cu", "xe_sched.cu", "batch.cu"]
+SOURCES = ["xengine.cu", "dump.cu", "corr.cu", "corr_static.cu", "xe_sched.cu", "batch.cu", "corner_turn.cu"]
 HEADERS = ["ptx.cuh", "xe_internal.h", "xe_sched.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
@@ -75,4 +75,4 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -58,6 +58,8 @@ ABI = [
     ("corr_batch_launch_count", _ll, [_vp]),
     ("corr_batch_destroy", None, [_vp]),
     ("corr_tuned_cover", _ci, [_ci, _ci]),
+    ("corr_corner_turn", _ci, [_vp, _vp, _ci, _ci, _ci, _vp]),
+    ("corr_push_block_tcn", _ci, [_vp, _vp, _vp]),
     ("corr_xcorr_static", _ci, [_vp, _ci, _ci, _ci, _ci, _vp, _vp]),
     ("corr_launch_count", _ll, [_vp]),
     ("corr_destroy", None, [_vp]),
@@ -148,6 +150,21 @@ def tuned_cover(n_in: int, block_len: int) -> int:
     return rc
 
 
+def corner_turn(x_tcn, out=None, stream=None):
+    """F-engine order uint8[block_len][n_chan][n_inputs] (CUDA tensor) to
+    X-engine order uint8[n_chan][n_inputs][block_len] via corr_corner_turn."""
+    import torch
+    if not (x_tcn.is_cuda and x_tcn.dtype == torch.uint8 and x_tcn.is_contiguous()
+            and x_tcn.dim() == 3):
+        raise ValueError("x_tcn must be a contiguous uint8 CUDA tensor [block_len][n_chan][n_inputs]")
+    T, C, N = x_tcn.shape
+    if out is None:
+        out = torch.empty((C, N, T), dtype=torch.uint8, device=x_tcn.device)
+    _ck(load().corr_corner_turn(x_tcn.data_ptr(), out.data_ptr(), N, C, T,
+                                _stream_handle(stream)), "corr_corner_turn")
+    return out
+
+
 def xcorr_static(block, n_ant: int, n_pol: int, vis=None, stream=None):
     """One block's visibilities through corr_xcorr_static (no allocation in the
     library): block is a uint8[n_chan][n_inputs][block_len] CUDA tensor, vis an
@@ -199,6 +216,16 @@ class Correlator:
         else:
             ptr = int(block)
         _ck(self._lib.corr_push_block(self._h, ptr, _stream_handle(stream)), "corr_push_block")
+
+    def push_block_tcn(self, block_tcn, stream=None):
+        """Integrates a block in F-engine order, uint8[block_len][n_chan][n_inputs]
+        (corner-turned on the device by the library)."""
+        import torch
+        if not (block_tcn.is_cuda and block_tcn.dtype == torch.uint8 and block_tcn.is_contiguous()
+                and block_tcn.numel() == self.n_chan * self.n_in * self.block_len):
+            raise ValueError("block_tcn must be a contiguous uint8 CUDA tensor of the context's size")
+        _ck(self._lib.corr_push_block_tcn(self._h, block_tcn.data_ptr(), _stream_handle(stream)),
+            "corr_push_block_tcn")
 
     def push_blocks(self, blocks, stream=None):
         """Integrates several blocks (device tensors or pointers) with shared folds."""

@@ -41,6 +41,7 @@ struct corr_ctx {
   uint32_t z_stage_bytes, pk_stage_bytes;
   int pitch;           // row pitch of the staged block (block_len rounded up to 16)
   uint8_t *d_pitched;  // [n_chan][n_in][pitch] when block_len % 16 != 0
+  uint8_t *d_turned;   // [n_chan][n_in][pitch]: corner-turned blocks (allocated on first use)
   long long samples;
   long long launches;
   unsigned long long timeout_ns;
@@ -79,6 +80,7 @@ int free_ctx(corr_ctx *ctx) {
     cudaFree(pl.d_cta_first);
   }
   cudaFree(ctx->d_pitched);
+  cudaFree(ctx->d_turned);
   for (int k = 0; k < 2; ++k) {
     cudaFree(ctx->d_stage[k]);
     if (ctx->ev_free[k]) cudaEventDestroy(ctx->ev_free[k]);
@@ -223,14 +225,13 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
   return CORR_OK;
 }
 
-int corr_push_blocks(corr_ctx *ctx, const uint8_t *const *d_blocks, int n_blocks,
-                     void *stream) {
-  if (!ctx || !d_blocks || n_blocks <= 0) return CORR_EINVAL;
-  for (int k = 0; k < n_blocks; ++k)
-    if (!d_blocks[k] || (reinterpret_cast<uintptr_t>(d_blocks[k]) & 15u) != 0) return CORR_EINVAL;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  static_assert(sizeof(CUtensorMap) == sizeof(xe::XMaps::m[0]), "tensor map size");
-  const int per = ctx->per_launch;
+}  // extern "C"
+
+namespace {
+
+// One CMAC launch over nb (<= per_launch) blocks whose rows are already
+// ctx->pitch bytes apart.
+int launch_staged(corr_ctx *ctx, const uint8_t *const *staged, int nb, cudaStream_t st) {
   XParams p;
   std::memset(&p, 0, sizeof(p));
   p.probs = ctx->d_prob;
@@ -240,33 +241,83 @@ int corr_push_blocks(corr_ctx *ctx, const uint8_t *const *d_blocks, int n_blocks
   p.pk_stages = ctx->pk_stages;
   p.z_stage_bytes = ctx->z_stage_bytes;
   p.pk_stage_bytes = ctx->pk_stage_bytes;
+  xe::XMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  int rc;
+  for (int k = 0; k < nb; ++k)
+    if ((rc = encode_block_map(ctx, staged[k], reinterpret_cast<CUtensorMap *>(maps.m[k]))) !=
+        CORR_OK)
+      return rc;
+  const ItemPlan &pl = ctx->plans[nb];
+  p.items = pl.d_items;
+  p.cta_first = pl.d_cta_first;
+  if ((rc = cuda_err(xe::launch_cmac(maps, p, pl.grid, ctx->smem_bytes, st))) != CORR_OK)
+    return rc;
+  ctx->launches++;
+  ctx->samples += (long long)nb * ctx->block_len;
+  return CORR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int corr_push_blocks(corr_ctx *ctx, const uint8_t *const *d_blocks, int n_blocks,
+                     void *stream) {
+  if (!ctx || !d_blocks || n_blocks <= 0) return CORR_EINVAL;
+  for (int k = 0; k < n_blocks; ++k)
+    if (!d_blocks[k] || (reinterpret_cast<uintptr_t>(d_blocks[k]) & 15u) != 0) return CORR_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  static_assert(sizeof(CUtensorMap) == sizeof(xe::XMaps::m[0]), "tensor map size");
+  const int per = ctx->per_launch;
   int rc;
   for (int k0 = 0; k0 < n_blocks; k0 += per) {
     const int nb = std::min(per, n_blocks - k0);
-    xe::XMaps maps;
-    std::memset(&maps, 0, sizeof(maps));
+    const uint8_t *staged[xe::kMaxBlocksPerLaunch];
     for (int k = 0; k < nb; ++k) {
-      const uint8_t *src = d_blocks[k0 + k];
+      staged[k] = d_blocks[k0 + k];
       if (ctx->d_pitched) {
-        if ((rc = cuda_err(xe::launch_pitch(src, ctx->d_pitched, (long long)ctx->n_chan * ctx->n_in,
-                                            ctx->block_len, ctx->pitch, st, ctx->n_sm * 8))) !=
-            CORR_OK)
+        if ((rc = cuda_err(xe::launch_pitch(staged[k], ctx->d_pitched,
+                                            (long long)ctx->n_chan * ctx->n_in, ctx->block_len,
+                                            ctx->pitch, st, ctx->n_sm * 8))) != CORR_OK)
           return rc;
         ctx->launches++;
-        src = ctx->d_pitched;
+        staged[k] = ctx->d_pitched;
       }
-      if ((rc = encode_block_map(ctx, src, reinterpret_cast<CUtensorMap *>(maps.m[k]))) != CORR_OK)
-        return rc;
     }
-    const ItemPlan &pl = ctx->plans[nb];
-    p.items = pl.d_items;
-    p.cta_first = pl.d_cta_first;
-    if ((rc = cuda_err(xe::launch_cmac(maps, p, pl.grid, ctx->smem_bytes, st))) != CORR_OK)
-      return rc;
-    ctx->launches++;
-    ctx->samples += (long long)nb * ctx->block_len;
+    if ((rc = launch_staged(ctx, staged, nb, st)) != CORR_OK) return rc;
   }
   return CORR_OK;
+}
+
+int corr_corner_turn(const uint8_t *d_src, uint8_t *d_dst, int n_in, int n_chan, int block_len,
+                     void *stream) {
+  if (!d_src || !d_dst || n_in <= 0 || n_chan <= 0 || block_len <= 0) return CORR_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_src) & 3u) || (reinterpret_cast<uintptr_t>(d_dst) & 3u))
+    return CORR_EINVAL;
+  int dev = 0, n_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return CORR_ECUDA;
+  return cuda_err(xe::launch_corner_turn(d_src, d_dst, n_in, n_chan, block_len, block_len,
+                                         static_cast<cudaStream_t>(stream), n_sm * 8));
+}
+
+int corr_push_block_tcn(corr_ctx *ctx, const uint8_t *d_src, void *stream) {
+  if (!ctx || !d_src || (reinterpret_cast<uintptr_t>(d_src) & 3u)) return CORR_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc;
+  if (!ctx->d_turned &&
+      (rc = cuda_err(cudaMalloc(&ctx->d_turned, (size_t)ctx->n_chan * ctx->n_in * ctx->pitch))) !=
+          CORR_OK)
+    return rc;
+  if ((rc = cuda_err(xe::launch_corner_turn(d_src, ctx->d_turned, ctx->n_in, ctx->n_chan,
+                                            ctx->block_len, ctx->pitch, st, ctx->n_sm * 8))) !=
+      CORR_OK)
+    return rc;
+  ctx->launches++;
+  const uint8_t *staged = ctx->d_turned;
+  return launch_staged(ctx, &staged, 1, st);
 }
 
 int corr_push_block(corr_ctx *ctx, const uint8_t *d_block, void *stream) {

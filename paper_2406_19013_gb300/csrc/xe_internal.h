@@ -128,5 +128,7 @@ cudaError_t launch_dump(int64_t *acc, int64_t *vis, int64_t *stokes, int n_ant, 
                         int n_chan, cudaStream_t stream, int grid);
 cudaError_t launch_pitch(const uint8_t *src, uint8_t *dst, long long rows, int T, int pitch,
                          cudaStream_t stream, int grid);
+cudaError_t launch_corner_turn(const uint8_t *src, uint8_t *dst, int n_in, int n_chan,
+                               int block_len, int dst_pitch, cudaStream_t stream, int grid);
 
 }  // namespace xe

@@ -309,3 +309,25 @@ def test_stokes_cross_pairs_from_full_matrix(oracle_mod, synth_mod):
                 got = st[c, p * (p + 1) // 2 + q]
                 for s in range(4):
                     assert complex(got[s, 0], got[s, 1]) == want[s]
+
+
+def test_corner_turn_handworked(oracle_mod):
+    # 3 samples x 2 channels x 2 inputs, every byte distinct: byte (t, c, i)
+    # = 16 t + 4 c + i; the turned block holds input i's samples of channel c
+    # in time order
+    x = np.array([[[16 * t + 4 * c + i for i in range(2)] for c in range(2)] for t in range(3)],
+                 dtype=np.uint8)
+    out = oracle_mod.corner_turn(x)
+    assert out.shape == (2, 2, 3)
+    assert out[1, 0].tolist() == [4, 20, 36]
+    assert out[0, 1].tolist() == [1, 17, 33]
+    assert np.array_equal(out, np.transpose(x, (1, 2, 0)))
+
+
+def test_corner_turn_feeds_the_correlation(oracle_mod, synth_mod):
+    # the turned F-engine-order block correlates exactly like the block
+    # generated in X-engine order
+    x = synth_mod.make_block(6, 3, 40, seed=8)
+    x_tcn = np.ascontiguousarray(np.transpose(x, (2, 0, 1)))
+    assert np.array_equal(oracle_mod.corner_turn(x_tcn), x)
+    assert np.array_equal(oracle_mod.xcorr(oracle_mod.corner_turn(x_tcn)), oracle_mod.xcorr(x))

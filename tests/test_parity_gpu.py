@@ -319,3 +319,40 @@ def test_large_n_sampled(corr, torch_cuda, oracle_mod, synth_mod):
     autos = _autos_numpy(x)
     diag = np.arange(w.n_in) * (np.arange(w.n_in) + 3) // 2
     assert np.array_equal(vis[:, diag, 0], autos)
+
+
+@pytest.mark.parametrize("T,C,N", [(1, 1, 1), (5, 3, 10), (128, 2, 128), (129, 3, 130),
+                                   (100, 7, 192), (1000, 2, 301), (2048, 4, 64), (257, 1, 1030)])
+def test_corner_turn_matches_oracle(corr, torch_cuda, oracle_mod, T, C, N):
+    torch = torch_cuda
+    rng = np.random.default_rng(T * 7 + C * 3 + N)
+    x_tcn = rng.integers(0, 256, size=(T, C, N), dtype=np.uint8)
+    got = corr.corner_turn(torch.from_numpy(x_tcn).cuda())
+    assert np.array_equal(got.cpu().numpy(), oracle_mod.corner_turn(x_tcn))
+
+
+@pytest.mark.parametrize("n_ant,n_pol,C,T", [(8, 2, 16, 1024), (65, 2, 3, 1000), (5, 1, 4, 33)])
+def test_push_block_tcn_matches_oracle(corr, torch_cuda, oracle_mod, synth_mod, n_ant, n_pol, C,
+                                       T):
+    torch = torch_cuda
+    n = n_ant * n_pol
+    blocks = [synth_mod.make_block(n, C, T, seed=30 + b, tones=synth_mod.random_phase_tone(n, 30))
+              for b in range(2)]
+    with corr.Correlator(n_ant, n_pol, C, T) as xc:
+        for x in blocks:
+            x_tcn = np.ascontiguousarray(np.transpose(x, (2, 0, 1)))  # F-engine order
+            xc.push_block_tcn(torch.from_numpy(x_tcn).cuda())
+        vis, _ = xc.dump()
+        xc.check()
+    assert np.array_equal(vis.cpu().numpy(),
+                          oracle_mod.xcorr(blocks[0]) + oracle_mod.xcorr(blocks[1]))
+
+
+def test_corner_turn_paper_block(corr, torch_cuda, oracle_mod, synth_mod):
+    # the full 1.61 GB block of the 192-input workload, in F-engine order
+    torch = torch_cuda
+    w = synth_mod.workload("paper", seed=12)
+    x = w.block(0)
+    x_tcn = np.ascontiguousarray(np.transpose(x, (2, 0, 1)))
+    got = corr.corner_turn(torch.from_numpy(x_tcn).cuda()).cpu().numpy()
+    assert np.array_equal(got, oracle_mod.corner_turn(x_tcn))
