@@ -68,6 +68,7 @@ extern "C" {
 #define CORR_MAX_INPUTS 8192
 
 typedef struct corr_ctx corr_ctx;
+typedef struct corr_server corr_server;
 
 /*
  * Creates a correlator for n_ant antennas with n_pol (1 or 2) polarisations,
@@ -323,6 +324,93 @@ int corr_tuned_cover(int n_in, int block_len);
 /* Releases everything the context owns.  The caller must have synchronised
  * every stream that used it.  NULL is ignored. */
 void corr_destroy(corr_ctx *ctx);
+
+/*
+ * Serving: a loop that takes blocks of several arrays as they arrive on the
+ * host and returns each completed integration's visibilities.
+ *
+ * The paper's system runs hashpipe threads around ring buffers: network
+ * input, GPU correlation and output (Sec. 2.3).  corr_server_create starts
+ * one worker thread that owns three CUDA streams, one each for
+ * host-to-device copies, correlation and device-to-host copies, plus:
+ *   - an arena of `arena_bytes` of device memory for block slots (first-fit
+ *     allocation; blocks wait in arrival order while it is full, so the
+ *     budget bounds the HBM in flight);
+ *   - per array, a context (resident int64 accumulators) and a pinned host
+ *     result buffer.
+ *
+ * Blocks carry (array, seq).  Integration k of an array holds sequence
+ * numbers [k L, (k + 1) L), L = blocks_per_integration (1..64).  Blocks may
+ * arrive in any order:
+ *   - A block up to `window` - 1 integrations ahead of the current one is
+ *     staged and held.
+ *   - A block `window` or more integrations ahead closes the integrations it
+ *     leaves behind.  A closed integration completes with the blocks it
+ *     holds; the rest count as dropped.
+ *   - Duplicates, and blocks of closed or finished integrations, are
+ *     discarded and counted.
+ * corr_server_flush closes every open integration.
+ */
+typedef struct {
+  int n_ant, n_pol, n_chan, block_len;
+  int blocks_per_integration;  /* L, 1..64 */
+} corr_array_desc;
+
+typedef struct {
+  int array;
+  long long integration;  /* k: sequence numbers [k L, (k + 1) L) */
+  int n_blocks;           /* blocks integrated (L unless some were dropped) */
+  uint64_t block_mask;    /* bit s: sequence number k L + s was integrated */
+  const int64_t *vis;     /* int64[n_chan][P][2] in a server-owned pinned buffer, valid
+                             until corr_server_release(array); NULL in dry mode */
+  double t_first_arrival_ms, t_last_arrival_ms, t_done_ms; /* steady clock */
+} corr_result;
+
+typedef struct {
+  long long submitted, integrated, duplicates, late, integrations, incomplete_integrations;
+  double latency_p50_ms, latency_p99_ms, latency_max_ms; /* block arrival -> result ready */
+  long long latency_samples;
+  size_t arena_peak_bytes;
+  int error; /* first error of the worker, CORR_OK if none */
+} corr_server_info;
+
+/* Dry mode: no device work at all (copies, pushes and dumps complete at once,
+ * results carry no visibilities); the admission and ordering policy runs
+ * unchanged, so it can be tested without a GPU. */
+#define CORR_SERVER_DRY 1
+
+/* Errors: CORR_EINVAL (sizes as for corr_create, L out of 1..64, window < 1,
+ * arena smaller than the largest block, unknown flag), CORR_EARCH,
+ * CORR_ENOMEM, CORR_ECUDA. */
+int corr_server_create(int n_arrays, const corr_array_desc *arrays, size_t arena_bytes, int window,
+                       int flags, corr_server **out);
+
+/* Queues block `seq` of `array` (uint8[n_chan][N][block_len] in host memory,
+ * pinned for full copy speed) and returns at once.  h_block must stay valid
+ * and unchanged until the integration that holds it has been returned by
+ * corr_server_poll, or the block was discarded, or the server is destroyed.
+ * Errors: CORR_EINVAL (bad array, negative seq, NULL block outside dry mode),
+ * or the worker's error. */
+int corr_server_submit(corr_server *s, int array, long long seq, const uint8_t *h_block);
+
+/* Moves up to max_results completed integrations into out[], oldest first,
+ * waiting up to timeout_ms for the first.  Returns how many, or a negative
+ * error (the worker's, or CORR_EINVAL). */
+int corr_server_poll(corr_server *s, corr_result *out, int max_results, int timeout_ms);
+
+/* The caller is done with the array's last result; its buffer may be reused
+ * for the next integration (which is held back until then). */
+int corr_server_release(corr_server *s, int array);
+
+/* Closes every open integration (see above). */
+int corr_server_flush(corr_server *s);
+
+/* Counters and latency percentiles so far. */
+int corr_server_stats(corr_server *s, corr_server_info *out);
+
+/* Stops the worker, waits for the device, frees everything.  Results not yet
+ * polled are lost.  NULL is ignored. */
+void corr_server_destroy(corr_server *s);
 
 /* Static string naming a CORR_* code. */
 const char *corr_strerror(int code);

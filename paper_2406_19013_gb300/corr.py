@@ -66,6 +66,40 @@ ABI = [
     ("corr_strerror", ctypes.c_char_p, [_ci]),
 ]
 
+class ArrayDesc(ctypes.Structure):
+    _fields_ = [("n_ant", ctypes.c_int), ("n_pol", ctypes.c_int), ("n_chan", ctypes.c_int),
+                ("block_len", ctypes.c_int), ("blocks_per_integration", ctypes.c_int)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("array", ctypes.c_int), ("integration", ctypes.c_longlong),
+                ("n_blocks", ctypes.c_int), ("block_mask", ctypes.c_uint64),
+                ("vis", ctypes.c_void_p), ("t_first_arrival_ms", ctypes.c_double),
+                ("t_last_arrival_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("integrated", ctypes.c_longlong),
+                ("duplicates", ctypes.c_longlong), ("late", ctypes.c_longlong),
+                ("integrations", ctypes.c_longlong),
+                ("incomplete_integrations", ctypes.c_longlong),
+                ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
+                ("latency_max_ms", ctypes.c_double), ("latency_samples", ctypes.c_longlong),
+                ("arena_peak_bytes", ctypes.c_size_t), ("error", ctypes.c_int)]
+
+
+ABI += [
+    ("corr_server_create", _ci, [_ci, ctypes.POINTER(ArrayDesc), ctypes.c_size_t, _ci, _ci,
+                                 ctypes.POINTER(_vp)]),
+    ("corr_server_submit", _ci, [_vp, _ci, _ll, _vp]),
+    ("corr_server_poll", _ci, [_vp, ctypes.POINTER(ServerResult), _ci, _ci]),
+    ("corr_server_release", _ci, [_vp, _ci]),
+    ("corr_server_flush", _ci, [_vp]),
+    ("corr_server_stats", _ci, [_vp, ctypes.POINTER(ServerInfo)]),
+    ("corr_server_destroy", None, [_vp]),
+]
+CORR_SERVER_DRY = 1
+
 _lock = threading.Lock()
 _lib = None
 
@@ -399,6 +433,98 @@ class Batch:
         if getattr(self, "_h", None):
             self._lib.corr_batch_destroy(self._h)
             self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """A served X-engine (corr_server_*): blocks of several arrays arrive one by
+    one from host memory; completed integrations come back from ``poll``.
+
+    ``arrays`` is a list of (n_ant, n_pol, n_chan, block_len,
+    blocks_per_integration).  ``submit(array, seq, block)`` takes a uint8
+    numpy array or CPU torch tensor of the array's block size (pinned memory
+    copies fastest); the Server keeps a reference until it is closed.
+    ``poll`` returns dicts with the integration's metadata and, unless dry, a
+    copy of its visibilities (int64[n_chan][P][2]); the server-side buffer is
+    released at once.
+    """
+
+    def __init__(self, arrays, arena_bytes: int, window: int = 2, dry: bool = False):
+        self._lib = load()
+        self.arrays = [tuple(int(v) for v in a) for a in arrays]
+        self.dry = dry
+        descs = (ArrayDesc * len(self.arrays))(*[ArrayDesc(*a) for a in self.arrays])
+        h = _vp()
+        _ck(self._lib.corr_server_create(len(self.arrays), descs, int(arena_bytes), window,
+                                         CORR_SERVER_DRY if dry else 0, ctypes.byref(h)),
+            "corr_server_create")
+        self._h = h
+        self._keep = []
+
+    def submit(self, array: int, seq: int, block=None):
+        ptr = None
+        if block is not None:
+            na, npol, nc, T, _ = self.arrays[array]
+            nbytes = nc * na * npol * T
+            if hasattr(block, "data_ptr"):
+                if block.is_cuda or block.numel() * block.element_size() != nbytes:
+                    raise ValueError("block must be a host tensor of the array's block size")
+                ptr = block.data_ptr()
+            else:
+                arr = np.asarray(block)
+                if arr.dtype != np.uint8 or arr.nbytes != nbytes or not arr.flags.c_contiguous:
+                    raise ValueError("block must be a contiguous uint8 array of the array's "
+                                     "block size")
+                ptr = arr.ctypes.data
+            self._keep.append(block)
+        _ck(self._lib.corr_server_submit(self._h, array, seq, ptr), "corr_server_submit")
+
+    def poll(self, max_results: int = 64, timeout_ms: int = 0, copy: bool = True):
+        """Completed integrations, oldest first.  With copy=False the
+        visibilities are not copied out ("vis" is None) and the server-side
+        buffer is released at once."""
+        out = (ServerResult * max_results)()
+        n = self._lib.corr_server_poll(self._h, out, max_results, timeout_ms)
+        if n < 0:
+            _ck(n, "corr_server_poll")
+        res = []
+        for r in out[:n]:
+            d = {"array": r.array, "integration": r.integration, "n_blocks": r.n_blocks,
+                 "block_mask": r.block_mask, "t_first_arrival_ms": r.t_first_arrival_ms,
+                 "t_last_arrival_ms": r.t_last_arrival_ms, "t_done_ms": r.t_done_ms, "vis": None}
+            if r.vis and copy:
+                na, npol, nc, T, _ = self.arrays[r.array]
+                shape = (nc, n_pairs(na * npol), 2)
+                buf = (ctypes.c_int64 * (shape[0] * shape[1] * 2)).from_address(r.vis)
+                d["vis"] = np.frombuffer(buf, dtype=np.int64).reshape(shape).copy()
+            _ck(self._lib.corr_server_release(self._h, r.array), "corr_server_release")
+            res.append(d)
+        return res
+
+    def flush(self):
+        _ck(self._lib.corr_server_flush(self._h), "corr_server_flush")
+
+    def stats(self) -> dict:
+        info = ServerInfo()
+        _ck(self._lib.corr_server_stats(self._h, ctypes.byref(info)), "corr_server_stats")
+        return {name: getattr(info, name) for name, _ in ServerInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.corr_server_destroy(self._h)
+            self._h = None
+            self._keep = []
 
     def __enter__(self):
         return self

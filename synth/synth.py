@@ -218,3 +218,29 @@ def pool_offsets(sizes, pool_bytes: int, seed: int = 4):
             raise ValueError("window larger than the pool")
         out.append(16 * int(rng.integers(0, span // 16 + 1)))
     return out
+
+
+# Input counts of the served workload: six arrays, dual polarisation
+SERVED_N = (32, 96, 192, 192, 384, 512)
+
+
+def served_arrays(seed: int = 6):
+    """Shapes of the served arrays: (n_ant, n_pol, n_chan, block_len) with the
+    input counts of SERVED_N, channel counts uniform in [64, 2048] and block
+    lengths uniform in [1024, 8192] on a 16-sample grid."""
+    rng = np.random.default_rng([seed, 0x5E4D])
+    out = []
+    for n in SERVED_N:
+        c = int(rng.integers(64, 2049))
+        t = 16 * int(rng.integers(64, 513))
+        out.append((n // 2, 2, c, t))
+    return out
+
+
+def poisson_requests(n: int, rate_per_s: float, n_arrays: int, seed: int):
+    """n requests (arrival time in s from the start, array index) of a Poisson
+    process of the given rate, each for an array drawn uniformly."""
+    rng = np.random.default_rng([seed, 0xA331])
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
+    a = rng.integers(0, n_arrays, size=n)
+    return [(float(ti), int(ai)) for ti, ai in zip(t, a)]
