@@ -412,6 +412,47 @@ int corr_server_stats(corr_server *s, corr_server_info *out);
  * polled are lost.  NULL is ignored. */
 void corr_server_destroy(corr_server *s);
 
+/*
+ * F-engine on the GPU (Sec. 2.1): polyphase filter bank, real FFT, EQ and
+ * 4+4-bit requantisation of 8-bit ADC samples, written in the X-engine's
+ * input order so the output feeds corr_push_block directly.
+ *
+ * For one input with samples x (a stream of (n_spectra + 3) * 2048 int8
+ * values), spectrum k (0 <= k < n_spectra) is
+ *     v_k[n] = sum_{j<4} h[2048 j + n] x[2048 (k + j) + n],      n < 2048
+ *     X_k[c] = sum_n v_k[n] exp(-2 pi i n c / 2048),               c < 1024
+ * with the 8192-tap prototype h[m] = w[m] sinc((m - 4096) / 2048), where
+ * w[m] = 0.54 - 0.46 cos(2 pi m / 8191) is the Hamming window (the paper's
+ * PFB size 2^11, 4 taps, Hamming window; FFT size 2^11).  With EQ gain
+ * g[i][c] the output byte is
+ *     out[c][i][k] = (q(g Re X) << 4) | (q(g Im X) & 15)
+ * where q rounds half away from zero and clips to [-7, 7].  Arithmetic is
+ * fp32, so a code can differ from the exact one only where g X lies within
+ * the fp32 rounding error of a quantisation boundary.
+ */
+#define CORR_FENGINE_POINTS 2048
+#define CORR_FENGINE_CHANNELS 1024
+#define CORR_FENGINE_TAPS 4
+typedef struct corr_fengine corr_fengine;
+
+/* n_in inputs, n_spectra spectra per run; EQ gains start at 1.
+ * Errors: CORR_EINVAL, CORR_EARCH, CORR_ENOMEM, CORR_ECUDA. */
+int corr_fengine_create(int n_in, int n_spectra, corr_fengine **out);
+
+/* Copies EQ gains float[n_in][1024] from host memory (synchronous). */
+int corr_fengine_set_eq(corr_fengine *f, const float *h_eq);
+
+/* d_adc: int8[n_in][(n_spectra + 3) * 2048] device samples (8-byte aligned);
+ * d_out: uint8[1024][n_in][n_spectra] device (16-byte aligned), overwritten.
+ * Stream-ordered and asynchronous.  Errors: CORR_EINVAL, CORR_ECUDA. */
+int corr_fengine_run(corr_fengine *f, const int8_t *d_adc, uint8_t *d_out, void *stream);
+
+/* As corr_fengine_run, but writes g X unquantised: float[1024][n_in][n_spectra][2]
+ * (real, imaginary).  For inspection and tests. */
+int corr_fengine_spectra(corr_fengine *f, const int8_t *d_adc, float *d_spec, void *stream);
+
+void corr_fengine_destroy(corr_fengine *f);
+
 /* Static string naming a CORR_* code. */
 const char *corr_strerror(int code);
 

@@ -99,6 +99,13 @@ ABI += [
     ("corr_server_destroy", None, [_vp]),
 ]
 CORR_SERVER_DRY = 1
+ABI += [
+    ("corr_fengine_create", _ci, [_ci, _ci, ctypes.POINTER(_vp)]),
+    ("corr_fengine_set_eq", _ci, [_vp, _vp]),
+    ("corr_fengine_run", _ci, [_vp, _vp, _vp, _vp]),
+    ("corr_fengine_spectra", _ci, [_vp, _vp, _vp, _vp]),
+    ("corr_fengine_destroy", None, [_vp]),
+]
 
 _lock = threading.Lock()
 _lib = None
@@ -525,6 +532,69 @@ class Server:
             self._lib.corr_server_destroy(self._h)
             self._h = None
             self._keep = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FEngine:
+    """The GPU F-engine (corr_fengine_*): int8 ADC streams
+    [n_in][(n_spectra + 3) * 2048] -> packed channel samples
+    uint8[1024][n_in][n_spectra], the X-engine's input order."""
+
+    def __init__(self, n_in: int, n_spectra: int, eq=None):
+        self._lib = load()
+        h = _vp()
+        _ck(self._lib.corr_fengine_create(n_in, n_spectra, ctypes.byref(h)), "corr_fengine_create")
+        self._h = h
+        self.n_in, self.n_spectra = n_in, n_spectra
+        if eq is not None:
+            self.set_eq(eq)
+
+    def set_eq(self, eq):
+        g = np.ascontiguousarray(eq, dtype=np.float32)
+        if g.shape != (self.n_in, 1024):
+            raise ValueError("eq must be float[n_in][1024]")
+        _ck(self._lib.corr_fengine_set_eq(self._h, g.ctypes.data), "corr_fengine_set_eq")
+
+    def _check_adc(self, adc):
+        import torch
+        if not (adc.is_cuda and adc.dtype == torch.int8 and adc.is_contiguous()
+                and adc.numel() == self.n_in * (self.n_spectra + 3) * 2048):
+            raise ValueError("adc must be a contiguous int8 CUDA tensor [n_in][(n_spectra+3)*2048]")
+
+    def run(self, adc, out=None, stream=None):
+        import torch
+        self._check_adc(adc)
+        if out is None:
+            out = torch.empty((1024, self.n_in, self.n_spectra), dtype=torch.uint8,
+                              device=adc.device)
+        _ck(self._lib.corr_fengine_run(self._h, adc.data_ptr(), out.data_ptr(),
+                                       _stream_handle(stream)), "corr_fengine_run")
+        return out
+
+    def spectra(self, adc, stream=None):
+        import torch
+        self._check_adc(adc)
+        out = torch.empty((1024, self.n_in, self.n_spectra, 2), dtype=torch.float32,
+                          device=adc.device)
+        _ck(self._lib.corr_fengine_spectra(self._h, adc.data_ptr(), out.data_ptr(),
+                                           _stream_handle(stream)), "corr_fengine_spectra")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.corr_fengine_destroy(self._h)
+            self._h = None
 
     def __enter__(self):
         return self

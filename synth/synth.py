@@ -244,3 +244,33 @@ def poisson_requests(n: int, rate_per_s: float, n_arrays: int, seed: int):
     t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
     a = rng.integers(0, n_arrays, size=n)
     return [(float(ti), int(ai)) for ti, ai in zip(t, a)]
+
+
+def adc_streams(n_in: int, n_samples: int, seed: int, sigma: float = 20.0,
+                tone_bins=(), tone_amp: float = 8.0, P: int = 2048) -> np.ndarray:
+    """8-bit ADC samples int8[n_in][n_samples]: Gaussian noise of standard
+    deviation sigma plus, for each entry of tone_bins, a sinusoid at that
+    channel centre (bin b of a P-point transform) with a random phase per
+    input; rounded half away from zero and clipped to [-128, 127]."""
+    rng = np.random.default_rng([seed, 0xADC0])
+    x = rng.normal(0.0, sigma, size=(n_in, n_samples))
+    t = np.arange(n_samples)
+    for b in tone_bins:
+        ph = rng.uniform(0.0, 2 * np.pi, size=(n_in, 1))
+        x += tone_amp * np.cos(2 * np.pi * b * t[None, :] / P + ph)
+    r = np.sign(x) * np.floor(np.abs(x) + 0.5)
+    return np.clip(r, -128, 127).astype(np.int8)
+
+
+def eq_for_noise(n_in: int, sigma: float, target_rms: float = 2.5,
+                 proto_sq_sum: float | None = None) -> np.ndarray:
+    """EQ gains float32[n_in][1024] that scale white noise of standard
+    deviation sigma to target_rms per real component after the filter bank
+    (rms per component = sigma sqrt(sum h^2 / 2))."""
+    if proto_sq_sum is None:
+        L = 4 * 2048
+        m = np.arange(L)
+        h = (0.54 - 0.46 * np.cos(2 * np.pi * m / (L - 1))) * np.sinc((m - L / 2) / 2048)
+        proto_sq_sum = float((h * h).sum())
+    g = target_rms / (sigma * np.sqrt(proto_sq_sum / 2.0))
+    return np.full((n_in, 1024), g, dtype=np.float32)
