@@ -477,7 +477,7 @@ def run_corner_turn(args):
     build.build()
     w = synth.workload("paper", seed=1)
     hb = torch.empty((N_CHAN, N_IN, BLOCK_LEN), dtype=torch.uint8, pin_memory=True)
-    w.block(0, out=hb.numpy())
+    w.block(0, n_chan=N_CHAN, out=hb.numpy())
     x = hb.to(dev)
     x_tcn = x.permute(2, 0, 1).contiguous()  # input preparation, not timed
     out = torch.empty_like(x)
@@ -517,7 +517,8 @@ def run_corner_turn(args):
         "unit": "GB/s", "n_gpus": 1, "steps": 4 * k, "warmup": args.warmup,
         "ms_per_step": ms_turn, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "uint8 [8192][1024][192] (F-engine order) -> [1024][192][8192]",
+        "config": {"workload": f"uint8 [8192][{N_CHAN}][192] (F-engine order) -> "
+                               f"[{N_CHAN}][192][8192]",
                    "bytes_per_step": nbytes, "l2": "inputs larger than L2 (1.61 GB)"},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                      "frac": gbs / hbm, "peak_source": f"{hbm_kind} copy bandwidth",
@@ -648,7 +649,7 @@ def run_fengine(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     build.build()
-    n_spec = BLOCK_LEN
+    n_spec = args.fe_spectra
     sigma = 20.0
     gen = torch.Generator(device=dev)
     gen.manual_seed(5)
@@ -673,7 +674,7 @@ def run_fengine(args):
 
     k = max(1, args.steps)
     ms_f = timed(lambda: fe.run(adc, out, stream), k)
-    xc = Correlator(N_ANT, N_POL, N_CHAN, BLOCK_LEN)
+    xc = Correlator(N_ANT, N_POL, N_CHAN, n_spec)
     ms_fx = timed(lambda: (fe.run(adc, out, stream), xc.push_block(out, stream)), k)
     xc.check()
     xc.close()
@@ -691,8 +692,8 @@ def run_fengine(args):
         "value": spectra_s, "unit": "spectra/s", "n_gpus": 1, "steps": k, "warmup": args.warmup,
         "ms_per_step": ms_f, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "192 inputs x 8192 spectra: int8 ADC streams -> uint8 "
-                               "[1024][192][8192] (X-engine order)",
+        "config": {"workload": f"192 inputs x {n_spec} spectra: int8 ADC streams -> uint8 "
+                               f"[1024][192][{n_spec}] (X-engine order)",
                    "adc_bytes": in_b, "out_bytes": out_b, "l2": "inputs larger than L2"},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                      "frac": gbs / hbm, "peak_source": f"{hbm_kind} copy bandwidth",
@@ -721,6 +722,8 @@ def main():
                          "correlators in shared launches; corner_turn: the device reorder "
                          "of F-engine-order blocks; served: arrivals from host memory, "
                          "latency percentiles; fengine: the GPU F-engine")
+    ap.add_argument("--fe-spectra", type=int, default=BLOCK_LEN,
+                    help="fengine workload: spectra per input (profiling a smaller run)")
     ap.add_argument("--n-chan", type=int, default=N_CHAN,
                     help="channels per GPU (profiling a smaller band; the reported workload is 1024)")
     args = ap.parse_args()
