@@ -252,6 +252,21 @@ int corr_corner_turn(const uint8_t *d_src, uint8_t *d_dst, int n_in, int n_chan,
  */
 int corr_push_block_tcn(corr_ctx *ctx, const uint8_t *d_src, void *stream);
 
+/*
+ * Failure-detection self-test.  Runs one CMAC launch over d_block (as for
+ * corr_push_block) in which the accumulator-draining warps first wait for a
+ * barrier that nothing ever completes.  That wait is bounded like every other
+ * device-side wait: after timeout_ms (1..10000) it gives up, raises the
+ * kernel's abort flag, and every role winds down.  The roles drain their own
+ * copies and tensor-core work, free TMEM and set the context's status word.
+ * Nothing is folded, so the integration buffer and the sample count are
+ * unchanged.  The next corr_check returns CORR_ETIMEOUT and clears the status;
+ * the context stays usable.  No fault, trap or unbounded wait is involved.
+ * Errors: CORR_EINVAL (NULL or misaligned pointer, timeout out of range),
+ * CORR_ECUDA.
+ */
+int corr_selftest_timeout(corr_ctx *ctx, const uint8_t *d_block, int timeout_ms, void *stream);
+
 /* Number of kernel launches the context has enqueued (pushes and dumps). */
 long long corr_launch_count(const corr_ctx *ctx);
 

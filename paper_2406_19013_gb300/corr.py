@@ -60,6 +60,7 @@ ABI = [
     ("corr_tuned_cover", _ci, [_ci, _ci]),
     ("corr_corner_turn", _ci, [_vp, _vp, _ci, _ci, _ci, _vp]),
     ("corr_push_block_tcn", _ci, [_vp, _vp, _vp]),
+    ("corr_selftest_timeout", _ci, [_vp, _vp, _ci, _vp]),
     ("corr_xcorr_static", _ci, [_vp, _ci, _ci, _ci, _ci, _vp, _vp]),
     ("corr_launch_count", _ll, [_vp]),
     ("corr_destroy", None, [_vp]),
@@ -333,6 +334,12 @@ class Correlator:
         return vis, stokes
 
     # ---------------------------------------------------------------- misc
+    def selftest_timeout(self, block, timeout_ms: int = 200, stream=None):
+        """Enqueues the failure-detection self-test (corr_selftest_timeout); the
+        next check() raises CorrError with CORR_ETIMEOUT."""
+        _ck(self._lib.corr_selftest_timeout(self._h, block.data_ptr(), timeout_ms,
+                                            _stream_handle(stream)), "corr_selftest_timeout")
+
     def check(self, stream=None):
         _ck(self._lib.corr_check(self._h, _stream_handle(stream)), "corr_check")
 

@@ -230,13 +230,16 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
 namespace {
 
 // One CMAC launch over nb (<= per_launch) blocks whose rows are already
-// ctx->pitch bytes apart.
-int launch_staged(corr_ctx *ctx, const uint8_t *const *staged, int nb, cudaStream_t st) {
+// ctx->pitch bytes apart.  selftest_timeout_ns > 0 runs the failure-detection
+// self-test instead (see corr_selftest_timeout).
+int launch_staged(corr_ctx *ctx, const uint8_t *const *staged, int nb, cudaStream_t st,
+                  unsigned long long selftest_timeout_ns = 0) {
   XParams p;
   std::memset(&p, 0, sizeof(p));
   p.probs = ctx->d_prob;
   p.status = ctx->d_status;
-  p.timeout_ns = ctx->timeout_ns;
+  p.timeout_ns = selftest_timeout_ns ? selftest_timeout_ns : ctx->timeout_ns;
+  p.selftest_never = selftest_timeout_ns ? 1 : 0;
   p.z_stages = ctx->z_stages;
   p.pk_stages = ctx->pk_stages;
   p.z_stage_bytes = ctx->z_stage_bytes;
@@ -254,7 +257,7 @@ int launch_staged(corr_ctx *ctx, const uint8_t *const *staged, int nb, cudaStrea
   if ((rc = cuda_err(xe::launch_cmac(maps, p, pl.grid, ctx->smem_bytes, st))) != CORR_OK)
     return rc;
   ctx->launches++;
-  ctx->samples += (long long)nb * ctx->block_len;
+  if (!selftest_timeout_ns) ctx->samples += (long long)nb * ctx->block_len;
   return CORR_OK;
 }
 
@@ -301,6 +304,24 @@ int corr_corner_turn(const uint8_t *d_src, uint8_t *d_dst, int n_in, int n_chan,
     return CORR_ECUDA;
   return cuda_err(xe::launch_corner_turn(d_src, d_dst, n_in, n_chan, block_len, block_len,
                                          static_cast<cudaStream_t>(stream), n_sm * 8));
+}
+
+int corr_selftest_timeout(corr_ctx *ctx, const uint8_t *d_block, int timeout_ms, void *stream) {
+  if (!ctx || !d_block || (reinterpret_cast<uintptr_t>(d_block) & 15u) || timeout_ms <= 0 ||
+      timeout_ms > 10000)
+    return CORR_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint8_t *staged = d_block;
+  int rc;
+  if (ctx->d_pitched) {
+    if ((rc = cuda_err(xe::launch_pitch(d_block, ctx->d_pitched, (long long)ctx->n_chan * ctx->n_in,
+                                        ctx->block_len, ctx->pitch, st, ctx->n_sm * 8))) !=
+        CORR_OK)
+      return rc;
+    ctx->launches++;
+    staged = ctx->d_pitched;
+  }
+  return launch_staged(ctx, &staged, 1, st, (unsigned long long)timeout_ms * 1000000ull);
 }
 
 int corr_push_block_tcn(corr_ctx *ctx, const uint8_t *d_src, void *stream) {

@@ -105,6 +105,7 @@ struct XParams {
   unsigned long long timeout_ns;
   int z_stages, pk_stages;
   uint32_t z_stage_bytes, pk_stage_bytes;
+  int selftest_never;  // failure-detection self-test (see corr_selftest_timeout)
 };
 
 // TMA descriptors (CUtensorMap, 128 bytes each), one per (problem, block) of

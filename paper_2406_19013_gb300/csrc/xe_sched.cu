@@ -136,7 +136,7 @@ bool stage_layout(const std::vector<const std::vector<XUnit> *> &unit_sets, int 
   L.z_stage_bytes = (uint32_t)round_up(max_zr * 128, 1024);
   L.pk_stage_bytes = (uint32_t)round_up(max_pk, 1024);  // swizzled TMA destination
   const int fixed = 1024 /* alignment slack */ + kBarrierBytes;
-  static_assert(8 * (2 * kMaxPkStages + 2 * kMaxZStages + 2 + kMmaWarps) + 16 <= kBarrierBytes,
+  static_assert(8 * (2 * kMaxPkStages + 2 * kMaxZStages + 2 + kMmaWarps + 1) + 16 <= kBarrierBytes,
                 "barrier area");
   const int avail = smem_optin - fixed;
   const int zb = (int)L.z_stage_bytes, pb = (int)L.pk_stage_bytes;

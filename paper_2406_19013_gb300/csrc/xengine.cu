@@ -82,7 +82,7 @@ __device__ __forceinline__ void decode_word(uint32_t w, uint2 &a, uint2 &q) {
 }
 
 struct Bars {
-  uint32_t pk_full, pk_empty, z_full, z_empty, acc_full, acc_empty, drain;
+  uint32_t pk_full, pk_empty, z_full, z_empty, acc_full, acc_empty, drain, never;
 };
 
 // Fire-and-forget 64-bit add in L2 (no return value, no round trip).
@@ -122,8 +122,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t *pk_buf = z_buf + (size_t)p.z_stages * p.z_stage_bytes;
   uint64_t *bar_mem = reinterpret_cast<uint64_t *>(pk_buf + (size_t)p.pk_stages * p.pk_stage_bytes);
   // [pk_full x S][pk_empty x S][z_full x Z][z_empty x Z][acc_full][acc_empty][drain x kMmaWarps]
+  // [never]: the last is only waited on by the failure-detection self-test
   uint32_t *misc = reinterpret_cast<uint32_t *>(bar_mem + 2 * p.pk_stages + 2 * p.z_stages + 2 +
-                                                kMmaWarps);
+                                                kMmaWarps + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(misc + 1);
   const uint32_t bar0 = smem_u32(bar_mem);
   Bars b;
@@ -134,6 +135,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   b.acc_full = b.z_empty + 8 * p.z_stages;
   b.acc_empty = b.acc_full + 8;
   b.drain = b.acc_empty + 8;
+  b.never = b.drain + 8 * kMmaWarps;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -149,6 +151,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(b.acc_full, kMmaWarps);
     mbar_init(b.acc_empty, kEpiWarps);
     for (int m = 0; m < kMmaWarps; ++m) mbar_init(b.drain + 8 * m, 1);
+    mbar_init(b.never, 1);  // nothing ever arrives here
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int k = 0; k < kMaxPkStages; ++k) armed[k] = 0, armed_ph[k] = 0;
       bool ok = true;
       int last_map = -1;
-      for (int it = it0; it < it1 && ok; it += it_step) {
+      for (int it = it0; it < it1 && ok && !*abort_flag; it += it_step) {
         const XItem item = item_at(p, it);
         const XProb pb = p.probs[item.prob];
         const XUnit *u = pb.units + item.tpl;
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t zph = 0;
       long long nu = 0;
       bool ok = true;
-      for (int it = it0; it < it1 && ok; it += it_step, ++nu) {
+      for (int it = it0; it < it1 && ok && !*abort_flag; it += it_step, ++nu) {
         const XItem item = item_at(p, it);
         const XProb pb = p.probs[item.prob];
         const XUnit *u = pb.units + item.tpl;
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int s = 0, zs = 0;
     uint32_t ph = 0, zph = 0;
     bool ok = true;
-    for (int it = it0; it < it1 && ok; it += it_step) {
+    for (int it = it0; it < it1 && ok && !*abort_flag; it += it_step) {
       const XItem item = item_at(p, it);
       const XProb pb = p.probs[item.prob];
       const XUnit *u = pb.units + item.tpl;
@@ -341,12 +344,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int rho = 32 * q + lane;
     const int g = rho >> 4, is_im = (rho >> 3) & 1, l = rho & 7;
     long long nu = 0;
+    // failure-detection self-test: wait for a barrier that nothing completes;
+    // the bounded wait gives up, raises the abort flag and every role winds
+    // down (nothing is folded)
+    if (p.selftest_never) mbar_wait(b.never, 0, abort_flag, to);
     for (int it = it0; it < it1; it += it_step, ++nu) {
       const XItem item = item_at(p, it);
       const XProb pb = p.probs[item.prob];
       const XUnit *u = pb.units + item.tpl;
       const int c = item.chan;
       if (!mbar_wait(b.acc_full, (uint32_t)(nu & 1), abort_flag, to)) break;
+      // once the kernel is winding down nothing more is folded: the
+      // integration is void and is reported as such
+      if (*abort_flag) break;
       tc_fence_after();
       const int n_seg = u->n_seg;
       for (int sg = 0; sg < n_seg; ++sg) {

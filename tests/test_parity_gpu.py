@@ -265,6 +265,34 @@ def test_channel_bands_on_two_streams(corr, torch_cuda, oracle_mod, synth_mod):
             xc.close()
 
 
+def test_device_wait_timeout_is_reported_and_the_context_recovers(corr, torch_cuda, oracle_mod,
+                                                                   synth_mod):
+    # A launch whose accumulator-draining warps wait on a barrier that nothing
+    # completes: the bounded wait gives up after 200 ms, the kernel winds down
+    # and reports through the status word; the context keeps integrating.
+    import time
+    torch = torch_cuda
+    x0 = synth_mod.make_block(16, 8, 1024, seed=90, tones=synth_mod.random_phase_tone(16, 90))
+    x1 = synth_mod.make_block(16, 8, 1024, seed=91, tones=synth_mod.random_phase_tone(16, 91))
+    with corr.Correlator(8, 2, 8, 1024) as xc:
+        d0, d1 = torch.from_numpy(x0).cuda(), torch.from_numpy(x1).cuda()
+        xc.push_block(d0)
+        xc.check()
+        t0 = time.time()
+        xc.selftest_timeout(d1, timeout_ms=200)
+        with pytest.raises(corr.CorrError) as err:
+            xc.check()
+        elapsed = time.time() - t0
+        assert err.value.code == corr.CORR_ETIMEOUT
+        assert 0.15 < elapsed < 10.0
+        xc.check()  # the status was cleared
+        assert xc.samples_integrated() == 1024  # nothing of the aborted launch counted
+        xc.push_block(d1)
+        vis, _ = xc.dump()
+        xc.check()
+    assert np.array_equal(vis.cpu().numpy(), oracle_mod.xcorr(x0) + oracle_mod.xcorr(x1))
+
+
 def _autos_numpy(x):
     s = x.astype(np.int8)
     re = (s >> 4).astype(np.int64)
