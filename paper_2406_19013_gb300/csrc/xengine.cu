@@ -81,6 +81,21 @@ __device__ __forceinline__ void decode_word(uint32_t w, uint2 &a, uint2 &q) {
   q = make_uint2(__byte_perm(im02, nre02, 0x7531), __byte_perm(im13, nre13, 0x7531));
 }
 
+// 16-byte shared-memory load and store on a 32-bit shared address.  The
+// operand buffers are carved from the dynamic shared memory by integer
+// alignment, so plain pointers into them would be generic pointers; these
+// keep the unpack's accesses on the shared-memory path.
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts128(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w));
+}
+
 struct Bars {
   uint32_t pk_full, pk_empty, z_full, z_empty, acc_full, acc_empty, drain, never;
 };
@@ -304,26 +319,26 @@ __global__ void __launch_bounds__(kThreads, 1)
             constexpr int R = 8 * kUnpackWarps;
             const int g = (tid >> 3) & 3, row0 = (tid & 7) | ((tid >> 5) << 3), sw = row0 & 7;
             // packed rows arrive 128B-swizzled: 16-byte chunk c of row r sits at c ^ (r & 7)
-            const uint8_t *src = pk + rg.pk_off + row0 * kPackedRowBytes + (((4 * sub + g) ^ sw) << 4);
+            const uint32_t src = smem_u32(pk) + rg.pk_off + row0 * kPackedRowBytes + (((4 * sub + g) ^ sw) << 4);
             const int rho0 = rg.interleaved ? (((row0 >> 3) << 4) | sw) : row0;
-            uint8_t *dst = zst + (size_t)(rg.z_row + rho0) * 128;
+            const uint32_t dst = smem_u32(zst) + (uint32_t)(rg.z_row + rho0) * 128u;
             const int off0 = ((2 * g) ^ sw) << 4, off1 = ((2 * g + 1) ^ sw) << 4;
             const int dst_step = (rg.interleaved ? 2 * R : R) * 128;  // R rows further on
             const int n_k = row0 < rg.n_in ? (rg.n_in - row0 + R - 1) / R : 0;
 #pragma unroll 2
             for (int kr = 0; kr < n_k; ++kr) {
-              const uint4 in = *reinterpret_cast<const uint4 *>(src + kr * R * kPackedRowBytes);
+              const uint4 in = lds128(src + kr * R * kPackedRowBytes);
               uint2 a0, q0, a1, q1, a2, q2, a3, q3;
               decode_word(in.x, a0, q0);
               decode_word(in.y, a1, q1);
               decode_word(in.z, a2, q2);
               decode_word(in.w, a3, q3);
-              uint8_t *d = dst + kr * dst_step;
-              *reinterpret_cast<uint4 *>(d + off0) = make_uint4(a0.x, a0.y, a1.x, a1.y);
-              *reinterpret_cast<uint4 *>(d + off1) = make_uint4(a2.x, a2.y, a3.x, a3.y);
+              const uint32_t d = dst + kr * dst_step;
+              sts128(d + off0, a0.x, a0.y, a1.x, a1.y);
+              sts128(d + off1, a2.x, a2.y, a3.x, a3.y);
               if (rg.interleaved) {
-                *reinterpret_cast<uint4 *>(d + 8 * 128 + off0) = make_uint4(q0.x, q0.y, q1.x, q1.y);
-                *reinterpret_cast<uint4 *>(d + 8 * 128 + off1) = make_uint4(q2.x, q2.y, q3.x, q3.y);
+                sts128(d + 8 * 128 + off0, q0.x, q0.y, q1.x, q1.y);
+                sts128(d + 8 * 128 + off1, q2.x, q2.y, q3.x, q3.y);
               }
             }
           }
