@@ -174,6 +174,7 @@ int tuned_cover(int n_in, int block_len, int n_sm, int smem_optin, int *rc) {
     goto done;
   for (int cv : cands) {
     const std::vector<xe::XUnit> units = xe::build_schedule(n_in, cv);
+    if (units.empty()) continue;
     const float ms = time_cover(units, n_in, C, T, n_sm, smem_optin, d_x, d_acc, d_status, st);
     if (ms >= 0.0f && (best_ms < 0.0f || ms < best_ms)) {
       best_ms = ms;
@@ -365,7 +366,7 @@ int corr_batch_create(int n_inst, const int *n_ant, const int *n_pol, const int 
   for (int k = 0; k < n_inst; ++k) {
     units[k] = xe::build_schedule(b->inst[k].n_in, b->inst[k].cover);
     xe::StageLayout L;
-    if (!xe::stage_layout({&units[k]}, optin, xe::kMaxZStages, &L)) {
+    if (units[k].empty() || !xe::stage_layout({&units[k]}, optin, xe::kMaxZStages, &L)) {
       free_batch(b);
       return CORR_EINVAL;
     }

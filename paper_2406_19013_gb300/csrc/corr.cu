@@ -152,6 +152,10 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
   }
 
   std::vector<XUnit> units = xe::build_schedule(ctx->n_in);
+  if (units.empty()) {
+    free_ctx(ctx);
+    return CORR_EINVAL;
+  }
   ctx->n_tpl = (int)units.size();
   xe::StageLayout L;
   if (!xe::stage_layout({&units}, smem_optin, xe::kMaxZStages, &L)) {
@@ -453,6 +457,7 @@ int corr_plan_items(int n_in, int n_chan, int block_len, int n_blocks, int cover
       (long long)n_blocks * block_len > CORR_MAX_BLOCK_LEN)
     return CORR_EINVAL;
   const std::vector<XUnit> units = xe::build_schedule(n_in, cover);
+  if (units.empty()) return CORR_EINVAL;
   std::vector<xe::XItem> it;
   std::vector<int> first;
   const int used = xe::build_items({{&units, n_chan, block_len, n_blocks}}, grid, it, first);
@@ -477,6 +482,7 @@ int corr_plan_cover(int n_in, int cover_kind, uint8_t *cover, int *n_units,
                     long long *issued_cmacs) {
   if (n_in <= 0 || n_in > CORR_MAX_INPUTS || cover_kind < 0 || cover_kind > 2) return CORR_EINVAL;
   std::vector<XUnit> units = xe::build_schedule(n_in, cover_kind);
+  if (units.empty()) return CORR_EINVAL;
   long long issued = 0;
   for (const XUnit &u : units) {
     for (int sg = 0; sg < u.n_seg; ++sg) {

@@ -30,6 +30,9 @@ constexpr int kWarpEpi0 = kUnpackWarps;
 constexpr int kWarpTma = kWarpEpi0 + kEpiWarps;
 constexpr int kWarpMma0 = kWarpTma + 1;
 constexpr int kThreads = 32 * (kWarpMma0 + kMmaWarps);
+// Largest region the unpack stages: each thread takes at most two rows of a
+// region per chunk (rows row0 and row0 + 8 kUnpackWarps).
+constexpr int kMaxRegionInputs = 2 * 8 * kUnpackWarps;
 // Pipeline depth limits and the shared-memory area for the barriers (full and
 // empty barrier per stage, accumulator full/empty, one drain barrier per MMA
 // issuer) and the TMEM address / abort flag behind them.

@@ -121,6 +121,11 @@ std::vector<XUnit> build_schedule(int N, int cover) {
   }
   std::stable_sort(units.begin(), units.end(),
                    [](const XUnit &a, const XUnit &b) { return a.work > b.work; });
+  // the unpack handles regions of at most kMaxRegionInputs inputs (every
+  // cover above satisfies this; an empty schedule reports a violation)
+  for (const XUnit &u : units)
+    for (int r = 0; r < u.n_reg; ++r)
+      if (u.reg[r].n_in > kMaxRegionInputs) return {};
   return units;
 }
 

@@ -325,9 +325,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int off0 = ((2 * g) ^ sw) << 4, off1 = ((2 * g + 1) ^ sw) << 4;
             const int dst_step = (rg.interleaved ? 2 * R : R) * 128;  // R rows further on
             const int n_k = row0 < rg.n_in ? (rg.n_in - row0 + R - 1) / R : 0;
-#pragma unroll 2
-            for (int kr = 0; kr < n_k; ++kr) {
-              const uint4 in = lds128(src + kr * R * kPackedRowBytes);
+            // a staged region holds at most 2 R rows, so a thread has at most
+            // two items per chunk: both loads go out before either decode
+            static_assert(2 * R >= 256, "two items per thread cover a 256-input region");
+            uint4 in0 = make_uint4(0u, 0u, 0u, 0u), in1 = in0;
+            if (n_k > 0) in0 = lds128(src);
+            if (n_k > 1) in1 = lds128(src + R * kPackedRowBytes);
+#pragma unroll
+            for (int kr = 0; kr < 2; ++kr) {
+              if (kr >= n_k) break;
+              const uint4 in = kr == 0 ? in0 : in1;
               uint2 a0, q0, a1, q1, a2, q2, a3, q3;
               decode_word(in.x, a0, q0);
               decode_word(in.y, a1, q1);
