@@ -304,7 +304,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nch = chunks_in_pk(pb, k % pb.pk_per_block);
         if (!mbar_wait(b.pk_full + 8 * s, ph, abort_flag, to)) { ok = false; break; }
         const uint8_t *pk = pk_buf + (size_t)s * p.pk_stage_bytes;
-        for (int sub = 0; sub < nch; ++sub) {
+#pragma unroll
+        for (int sub = 0; sub < kChunksPerPk; ++sub) {
+          if (sub >= nch) break;
           if (!mbar_wait(b.z_empty + 8 * zs, zph ^ 1u, abort_flag, to)) { ok = false; break; }
           uint8_t *zst = z_buf + (size_t)zs * p.z_stage_bytes;
           // operand chunk `sub` of the packed stage (64 of its 128 samples)
