@@ -95,6 +95,12 @@ __device__ __forceinline__ uint4 lds128(uint32_t a) {
 __device__ __forceinline__ void sts128(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w));
 }
+// As sts128, 1024 bytes (eight 128-byte operand rows) further on.
+__device__ __forceinline__ void sts128_q(uint32_t a, uint32_t x, uint32_t y, uint32_t z,
+                                        uint32_t w) {
+  asm volatile("st.shared.v4.b32 [%0+1024], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z),
+               "r"(w));
+}
 
 struct Bars {
   uint32_t pk_full, pk_empty, z_full, z_empty, acc_full, acc_empty, drain, never;
@@ -289,7 +295,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp < kUnpackWarps) {
     // ------------------------------------------------------------ unpack
+    // Thread tid owns rows row0 + R k of every staged region (R = 8 *
+    // kUnpackWarps rows per pass) and the 16-sample group g of each chunk;
+    // the 8 lanes of a quarter-warp share g and take 8 consecutive rows, so
+    // their swizzled 16-byte accesses fall on 8 different bank groups.
+    constexpr int R = 8 * kUnpackWarps;
+    // a staged region holds at most 2 R rows, so a thread has at most two
+    // items per chunk: both loads go out before either decode
+    static_assert(2 * R >= kMaxRegionInputs, "two items per thread cover a region");
     const int tid = threadIdx.x;
+    const int g = (tid >> 3) & 3, row0 = (tid & 7) | ((tid >> 5) << 3), sw = row0 & 7;
+    // packed rows arrive 128B-swizzled: 16-byte chunk c of row r sits at
+    // c ^ (r & 7); operand chunk `sub` of a stage is chunks 4 sub + g
+    const uint32_t src_sub0 = (uint32_t)((g ^ sw) << 4), src_sub1 = (uint32_t)(((4 + g) ^ sw) << 4);
+    const uint32_t off0 = (uint32_t)(((2 * g) ^ sw) << 4), off1 = (uint32_t)(((2 * g + 1) ^ sw) << 4);
+    const uint32_t pk_s0 = smem_u32(pk_buf), z_s0 = smem_u32(z_buf);
     int s = 0, zs = 0;
     uint32_t ph = 0, zph = 0;
     bool ok = true;
@@ -298,56 +318,53 @@ __global__ void __launch_bounds__(kThreads, 1)
       const XProb pb = p.probs[item.prob];
       const XUnit *u = pb.units + item.tpl;
       const int n_reg = u->n_reg;
-      // the (at most two) staged regions, held in registers
-      const XRegion rg0 = u->reg[0], rg1 = u->reg[n_reg > 1 ? 1 : 0];
+      // per-region constants of this thread (at most two regions)
+      uint32_t src_off[2], dst_off[2], dst_step[2];
+      int n_k[2], il[2];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const XRegion rg = u->reg[r < n_reg ? r : 0];
+        il[r] = rg.interleaved;
+        const int rho0 = rg.interleaved ? (((row0 >> 3) << 4) | sw) : row0;
+        src_off[r] = (uint32_t)(rg.pk_off + row0 * kPackedRowBytes);
+        dst_off[r] = (uint32_t)(rg.z_row + rho0) * 128u;
+        dst_step[r] = (uint32_t)((rg.interleaved ? 2 * R : R) * 128);  // R rows further on
+        n_k[r] = r < n_reg && row0 < rg.n_in ? (rg.n_in - row0 + R - 1) / R : 0;
+      }
       for (int k = item.pk0; k < item.pk0 + item.npk && ok; ++k) {
         const int nch = chunks_in_pk(pb, k % pb.pk_per_block);
         if (!mbar_wait(b.pk_full + 8 * s, ph, abort_flag, to)) { ok = false; break; }
-        const uint8_t *pk = pk_buf + (size_t)s * p.pk_stage_bytes;
+        const uint32_t pk_s = pk_s0 + (uint32_t)s * p.pk_stage_bytes;
 #pragma unroll
         for (int sub = 0; sub < kChunksPerPk; ++sub) {
           if (sub >= nch) break;
           if (!mbar_wait(b.z_empty + 8 * zs, zph ^ 1u, abort_flag, to)) { ok = false; break; }
-          uint8_t *zst = z_buf + (size_t)zs * p.z_stage_bytes;
+          const uint32_t z_s = z_s0 + (uint32_t)zs * p.z_stage_bytes;
           // operand chunk `sub` of the packed stage (64 of its 128 samples)
 #pragma unroll
           for (int r = 0; r < 2; ++r) {
             if (r >= n_reg) break;
-            const XRegion &rg = r == 0 ? rg0 : rg1;
-            // Thread tid owns rows row0 + R k (R = 8 * kUnpackWarps rows per
-            // pass) and the 16-sample group g of each; the 8 lanes of a
-            // quarter-warp share g and take 8 consecutive rows, so their
-            // swizzled 16-byte accesses fall on 8 different bank groups.
-            constexpr int R = 8 * kUnpackWarps;
-            const int g = (tid >> 3) & 3, row0 = (tid & 7) | ((tid >> 5) << 3), sw = row0 & 7;
-            // packed rows arrive 128B-swizzled: 16-byte chunk c of row r sits at c ^ (r & 7)
-            const uint32_t src = smem_u32(pk) + rg.pk_off + row0 * kPackedRowBytes + (((4 * sub + g) ^ sw) << 4);
-            const int rho0 = rg.interleaved ? (((row0 >> 3) << 4) | sw) : row0;
-            const uint32_t dst = smem_u32(zst) + (uint32_t)(rg.z_row + rho0) * 128u;
-            const int off0 = ((2 * g) ^ sw) << 4, off1 = ((2 * g + 1) ^ sw) << 4;
-            const int dst_step = (rg.interleaved ? 2 * R : R) * 128;  // R rows further on
-            const int n_k = row0 < rg.n_in ? (rg.n_in - row0 + R - 1) / R : 0;
-            // a staged region holds at most 2 R rows, so a thread has at most
-            // two items per chunk: both loads go out before either decode
-            static_assert(2 * R >= 256, "two items per thread cover a 256-input region");
+            const uint32_t src = pk_s + src_off[r] + (sub ? src_sub1 : src_sub0);
+            const uint32_t dst = z_s + dst_off[r];
             uint4 in0 = make_uint4(0u, 0u, 0u, 0u), in1 = in0;
-            if (n_k > 0) in0 = lds128(src);
-            if (n_k > 1) in1 = lds128(src + R * kPackedRowBytes);
+            if (n_k[r] > 0) in0 = lds128(src);
+            if (n_k[r] > 1) in1 = lds128(src + R * kPackedRowBytes);
 #pragma unroll
             for (int kr = 0; kr < 2; ++kr) {
-              if (kr >= n_k) break;
+              if (kr >= n_k[r]) break;
               const uint4 in = kr == 0 ? in0 : in1;
               uint2 a0, q0, a1, q1, a2, q2, a3, q3;
               decode_word(in.x, a0, q0);
               decode_word(in.y, a1, q1);
               decode_word(in.z, a2, q2);
               decode_word(in.w, a3, q3);
-              const uint32_t d = dst + kr * dst_step;
-              sts128(d + off0, a0.x, a0.y, a1.x, a1.y);
-              sts128(d + off1, a2.x, a2.y, a3.x, a3.y);
-              if (rg.interleaved) {
-                sts128(d + 8 * 128 + off0, q0.x, q0.y, q1.x, q1.y);
-                sts128(d + 8 * 128 + off1, q2.x, q2.y, q3.x, q3.y);
+              const uint32_t d0 = dst + (kr ? dst_step[r] : 0u) + off0;
+              const uint32_t d1 = dst + (kr ? dst_step[r] : 0u) + off1;
+              sts128(d0, a0.x, a0.y, a1.x, a1.y);
+              sts128(d1, a2.x, a2.y, a3.x, a3.y);
+              if (il[r]) {  // the Q rows follow 8 rows (1024 bytes) after the A rows
+                sts128_q(d0, q0.x, q0.y, q1.x, q1.y);
+                sts128_q(d1, q2.x, q2.y, q3.x, q3.y);
               }
             }
           }
