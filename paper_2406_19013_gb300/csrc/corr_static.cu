@@ -159,7 +159,7 @@ extern "C" int corr_xcorr_static(const uint8_t *d_block, int n_ant, int n_pol, i
   const int optin = g_smem_optin[dev];
   const int z_bytes = (max_z * 128 + 1023) / 1024 * 1024;
   const int pk_bytes = (max_pk + 1023) / 1024 * 1024;
-  const int fixed = 1024 + 256;
+  const int fixed = 1024 + xe::kBarrierBytes;
   int pk_stages = 3, z_stages = 0;
   for (int ps = 3; ps >= 2 && z_stages < 2; --ps) {
     pk_stages = ps;

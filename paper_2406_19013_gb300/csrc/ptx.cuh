@@ -148,6 +148,20 @@ __device__ __forceinline__ void mma_f8_ss(uint32_t d_tmem, uint64_t a_desc, uint
       : "memory");
 }
 
+// As mma_f8_ss, with each descriptor given as its low and high 32-bit words
+// (the caller keeps them in registers and advances the start address, the low
+// 14 bits, by plain 32-bit adds).
+__device__ __forceinline__ void mma_f8_ss_w(uint32_t d_tmem, uint32_t a_lo, uint32_t a_hi,
+                                           uint32_t b_lo, uint32_t b_hi, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\n.reg .b64 da, db;\nsetp.ne.b32 p, %6, 0;\n"
+      "mov.b64 da, {%1, %2};\nmov.b64 db, {%3, %4};\n"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], da, db, %5, p;\n}" ::"r"(d_tmem),
+      "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // The mbarrier receives one arrive once every tcgen05 operation this thread
 // issued before the commit has completed.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -183,6 +197,14 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr, uint32_t sbo) {
   d |= (uint64_t)1 << 46;                             // descriptor version
   d |= (uint64_t)2 << 61;                             // 128-byte swizzle
   return d;
+}
+
+// The two 32-bit words of sdesc_sw128(saddr, sbo).
+__device__ __forceinline__ uint32_t sdesc_sw128_lo(uint32_t saddr) {
+  return ((saddr & 0x3FFFFu) >> 4) | (1u << 16);
+}
+__device__ __forceinline__ uint32_t sdesc_sw128_hi(uint32_t sbo) {
+  return ((sbo & 0x3FFFFu) >> 4) | (1u << 14) | (2u << 29);
 }
 
 // Instruction descriptor, kind::f16: fp16 A and B (K-major), fp32 D.

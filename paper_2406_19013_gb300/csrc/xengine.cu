@@ -255,33 +255,44 @@ __global__ void __launch_bounds__(kThreads, 1)
         const XUnit *u = pb.units + item.tpl;
         const int n_seg = u->n_seg;
         static_assert(kMaxSegs / kMmaWarps == 2, "two segments per issuer at most");
-        // the (at most two) segments this issuer owns, held in registers
-        XSeg mine0 = u->seg[m < n_seg ? m : 0], mine1 = u->seg[m + kMmaWarps < n_seg ? m + kMmaWarps : 0];
+        // The (at most two) segments this issuer owns.  Their descriptors are
+        // built once per item, for Z stage 0 and K slice 0, as 32-bit words:
+        // a chunk in Z stage zs and K slice kk only adds (zs z_stage_bytes +
+        // 32 kk) / 16 to the start-address field, so each MMA costs an add
+        // or two and the instruction itself.  (One issuing thread shares its
+        // SM sub-partition with four unpack warps; the fewer instructions it
+        // needs per MMA, the sooner each MMA is issued.)
         const int n_mine = (m < n_seg) + (m + kMmaWarps < n_seg);
+        uint32_t d_col[2], idesc[2], a_lo[2], b_lo[2], b_hi[2];
+        const uint32_t z0 = smem_u32(z_buf), a_hi = sdesc_sw128_hi(1024u);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const XSeg &sgm = u->seg[j < n_mine ? m + kMmaWarps * j : 0];
+          d_col[j] = tmem + (uint32_t)sgm.tmem_col;
+          idesc[j] = idesc_e5m2_f32(128, sgm.n);
+          a_lo[j] = sdesc_sw128_lo(z0 + (uint32_t)sgm.a_zrow * 128u);
+          b_lo[j] = sdesc_sw128_lo(z0 + (uint32_t)sgm.b_zrow * 128u);
+          b_hi[j] = sdesc_sw128_hi((uint32_t)sgm.b_sbo);
+        }
         if (nu > 0 && !mbar_wait(b.acc_empty, (uint32_t)((nu - 1) & 1), abort_flag, to)) break;
         tc_fence_after();
-        bool first = true;  // the item's first chunk overwrites the accumulators
+        uint32_t acc0 = 0;  // the item's first MMA of each accumulator overwrites it
         for (int k = item.pk0; k < item.pk0 + item.npk && ok; ++k) {
           const int nch = chunks_in_pk(pb, k % pb.pk_per_block);
           for (int sub = 0; sub < nch; ++sub) {
             if (!mbar_wait(b.z_full + 8 * zs, zph, abort_flag, to)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t zb = smem_u32(z_buf + (size_t)zs * p.z_stage_bytes);
+            const uint32_t zoff = ((uint32_t)zs * p.z_stage_bytes) >> 4;
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
               if (j >= n_mine) break;
-              const XSeg &sgm = j == 0 ? mine0 : mine1;
-              const uint32_t idesc = idesc_e5m2_f32(128, sgm.n);
-              const uint32_t a0 = zb + (uint32_t)sgm.a_zrow * 128u;
-              const uint32_t b0 = zb + (uint32_t)sgm.b_zrow * 128u;
+              const uint32_t al = a_lo[j] + zoff, bl = b_lo[j] + zoff;
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t da = sdesc_sw128(a0 + 32u * kk, 1024u);
-                const uint64_t db = sdesc_sw128(b0 + 32u * kk, (uint32_t)sgm.b_sbo);
-                mma_f8_ss(tmem + (uint32_t)sgm.tmem_col, da, db, idesc, !(first && kk == 0));
-              }
+              for (int kk = 0; kk < 4; ++kk)
+                mma_f8_ss_w(d_col[j], al + 2u * kk, a_hi, bl + 2u * kk, b_hi[j], idesc[j],
+                            kk ? 1u : acc0);
             }
-            first = false;
+            acc0 = 1;
             mma_commit(b.z_empty + 8 * zs);
             if (++zs == p.z_stages) { zs = 0; zph ^= 1u; }
           }
