@@ -21,11 +21,13 @@
 //     segments of overlap at the tile start);
 //   - spectra go through in batches of kBatch, so that every barrier of the
 //     FFT is shared by kBatch independent butterflies per thread;
-//   - thread t filters samples 8 t .. 8 t + 7, holding its 32 filter
-//     coefficients in registers, and pairs them as z[m] = v[2m] + i v[2m+1];
-//   - a 1024-point complex FFT (five radix-4 stages, base-4 digit-reversed
-//     input) runs in shared memory, then the standard split gives the 2048-point
-//     real FFT's channels 0..1023;
+//   - thread t filters samples 4 t .. 4 t + 3 and 1024 + 4 t .. + 3, holding
+//     its 32 filter coefficients in registers, and pairs them as
+//     z[m] = v[2m] + i v[2m+1];
+//   - a 1024-point complex FFT runs in three in-place passes over shared
+//     memory, 1024 = 16 x 4 x 16 (each thread does a 16-point FFT in registers
+//     in the first and last pass, four 4-point FFTs in the middle one), then
+//     the standard split gives the 2048-point real FFT's channels 0..1023;
 //   - EQ and requantisation produce one byte per channel into a staging tile
 //     [kSpecTile spectra][1024 channels], written out as 32-byte runs of
 //     out[c][input][k0 ..].
@@ -54,15 +56,47 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// base-4 digit reversal of a 10-bit index (five digits)
-__device__ __forceinline__ int digitrev4(int m) {
-  int r = 0;
+// Forward 4-point DFT in place: X[k] = sum_n a[n] (-i)^(n k).
+__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
+  const float2 s02 = make_float2(a0.x + a2.x, a0.y + a2.y);
+  const float2 d02 = make_float2(a0.x - a2.x, a0.y - a2.y);
+  const float2 s13 = make_float2(a1.x + a3.x, a1.y + a3.y);
+  const float2 d13 = make_float2(a1.x - a3.x, a1.y - a3.y);
+  a0 = make_float2(s02.x + s13.x, s02.y + s13.y);
+  a1 = make_float2(d02.x + d13.y, d02.y - d13.x);  // a0 - i a1 - a2 + i a3
+  a2 = make_float2(s02.x - s13.x, s02.y - s13.y);
+  a3 = make_float2(d02.x - d13.y, d02.y + d13.x);  // a0 + i a1 - a2 - i a3
+}
+
+// Forward 16-point DFT in place, natural order in and out:
+// Y[ka + 4 kb] = sum_nb W4^(nb kb) W16^(nb ka) sum_na a[4 na + nb] W4^(na ka).
+__device__ __forceinline__ void dft16(float2 (&a)[16]) {
+  constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f;  // cos, sin (pi/8)
+  constexpr float r2 = 0.70710678118654752f;
 #pragma unroll
-  for (int d = 0; d < 5; ++d) {
-    r = (r << 2) | (m & 3);
-    m >>= 2;
-  }
-  return r;
+  for (int nb = 0; nb < 4; ++nb) dft4(a[nb], a[4 + nb], a[8 + nb], a[12 + nb]);
+  // a[4 ka + nb] now holds T[nb][ka]; twiddle by W16^(nb ka) (literal constants)
+  a[5] = cmul(a[5], make_float2(c1, -s1));     // W16^1
+  a[6] = cmul(a[6], make_float2(r2, -r2));     // W16^2
+  a[7] = cmul(a[7], make_float2(s1, -c1));     // W16^3
+  a[9] = cmul(a[9], make_float2(r2, -r2));     // W16^2
+  a[10] = make_float2(a[10].y, -a[10].x);      // W16^4 = -i
+  a[11] = cmul(a[11], make_float2(-r2, -r2));  // W16^6
+  a[13] = cmul(a[13], make_float2(s1, -c1));   // W16^3
+  a[14] = cmul(a[14], make_float2(-r2, -r2));  // W16^6
+  a[15] = cmul(a[15], make_float2(-c1, s1));   // W16^9
+  // 4-point DFTs over nb for each ka: outputs Y[ka + 4 kb] land in a[4 ka + kb]
+#pragma unroll
+  for (int ka = 0; ka < 4; ++ka) dft4(a[4 * ka], a[4 * ka + 1], a[4 * ka + 2], a[4 * ka + 3]);
+  // transpose 4 x 4 so that a[k] = Y[k]
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 4; ++j) {
+      const float2 t = a[4 * i + j];
+      a[4 * i + j] = a[4 * j + i];
+      a[4 * j + i] = t;
+    }
 }
 
 __device__ __forceinline__ int quant(float a) {
@@ -75,21 +109,25 @@ __device__ __forceinline__ int quant(float a) {
 constexpr int kBatch = 4;                         // spectra per inner iteration
 constexpr int kRing = 8;                          // ring slots (>= kTaps - 1 + kBatch)
 constexpr int kRingBytes = kRing * kP;            // 16 KB
-// FFT buffers are padded by one element per 16 (element i at i + i / 16),
-// which keeps the radix-4 stages, the digit-reversed stores and the split's
-// reads at or near the two shared-memory wavefronts a float2 access needs.
-constexpr int kBufElems = kHalf + kHalf / 16;
+// FFT buffers: element e of a spectrum sits at 64 (e / 64) + ((e % 64) ^
+// (e / 64 % 16)).  The XOR keeps every access pattern of the passes at the
+// two shared-memory wavefronts a warp's float2 access needs: runs of 32
+// consecutive elements (the FIR's stores, the first pass's loads, the last
+// pass, the split) and stride-64 gathers (the first pass's stores and the
+// middle pass) alike; pairs (2k, 2k + 1) stay in one 16-byte slot, swapped
+// when the XOR is odd.
+constexpr int kBufElems = kHalf;
 constexpr int kBufBytes = kBatch * kBufElems * 8;
 constexpr int kStageBytes = kHalf * kSpecTile;    // 32 KB, [spectrum][channel]
 
-__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+__device__ __forceinline__ int swz(int e) { return (e & ~63) | ((e & 63) ^ ((e >> 6) & 15)); }
 static_assert(kSpecTile % kBatch == 0, "tile of whole batches");
 static_assert(kRing >= kTaps - 1 + kBatch && (kRing & (kRing - 1)) == 0, "ring size");
 
 // kQuant: 1 -> packed codes via the staging tile; 0 -> float2 g X straight to
 // global (X-engine order, for tolerance checks).
 template <int kQuant>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
     fengine_kernel(const int8_t *__restrict__ adc, const float *__restrict__ proto,
                    const float2 *__restrict__ tw_fft, const float2 *__restrict__ tw_split,
                    const float *__restrict__ eq, uint8_t *__restrict__ out_codes,
@@ -100,12 +138,6 @@ __global__ void __launch_bounds__(kThreads)
   uint8_t *stage = fe_smem + kRingBytes + kBufBytes;               // [kSpecTile][kHalf]
   const int tid = threadIdx.x;
   const int n_tiles = (n_spec + kSpecTile - 1) / kSpecTile;
-  // filter coefficients of this thread's 8 samples, all four taps
-  float hc[kTaps][8];
-#pragma unroll
-  for (int j = 0; j < kTaps; ++j)
-#pragma unroll
-    for (int e = 0; e < 8; ++e) hc[j][e] = __ldg(proto + j * kP + 8 * tid + e);
   const long long stream_len = (long long)(n_spec + kTaps - 1) * kP;
 
   for (long long w = blockIdx.x; w < (long long)n_in * n_tiles; w += gridDim.x) {
@@ -113,9 +145,9 @@ __global__ void __launch_bounds__(kThreads)
     const int k0 = tile * kSpecTile;
     const int ns = min(kSpecTile, n_spec - k0);
     const int8_t *x = adc + (long long)in * stream_len;
-    float g[4];  // EQ gains of this thread's channels 4 tid .. 4 tid + 3
+    float g[4];  // EQ gains of this thread's channels tid + 256 e
 #pragma unroll
-    for (int e = 0; e < 4; ++e) g[e] = __ldg(eq + (long long)in * kHalf + 4 * tid + e);
+    for (int e = 0; e < 4; ++e) g[e] = __ldg(eq + (long long)in * kHalf + tid + kThreads * e);
     // prime the ring with segments k0 .. k0 + 2
     for (int j = 0; j < kTaps - 1; ++j)
       *reinterpret_cast<uint2 *>(&ring[((k0 + j) & (kRing - 1)) * kP + 8 * tid]) =
@@ -129,7 +161,21 @@ __global__ void __launch_bounds__(kThreads)
             __ldg(reinterpret_cast<const uint2 *>(x + (long long)seg * kP + 8 * tid));
       }
       __syncthreads();
-      // ---- polyphase FIR of each spectrum of the batch
+      // ---- polyphase FIR of each spectrum of the batch.  The filter
+      // coefficients of this thread's 8 samples (4 tid .. + 3 and 1024 + 4 tid
+      // .. + 3 of the 2048), all four taps, are re-read (from L1) per batch,
+      // so that they do not stay live through the FFT passes.
+      float hc[kTaps][8];
+#pragma unroll
+      for (int j = 0; j < kTaps; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float4 c4 = __ldg(reinterpret_cast<const float4 *>(proto + j * kP + h * kHalf + 4 * tid));
+          hc[j][4 * h] = c4.x;
+          hc[j][4 * h + 1] = c4.y;
+          hc[j][4 * h + 2] = c4.z;
+          hc[j][4 * h + 3] = c4.w;
+        }
 #pragma unroll
       for (int u = 0; u < kBatch; ++u) {
         if (u >= nb) break;
@@ -139,71 +185,99 @@ __global__ void __launch_bounds__(kThreads)
         for (int e = 0; e < 8; ++e) v[e] = 0.0f;
 #pragma unroll
         for (int j = 0; j < kTaps; ++j) {
-          const uint2 raw =
-              *reinterpret_cast<const uint2 *>(&ring[((k + j) & (kRing - 1)) * kP + 8 * tid]);
-          const uint32_t wd[2] = {raw.x, raw.y};
+          const int8_t *seg = &ring[((k + j) & (kRing - 1)) * kP];
+          const uint32_t wd[2] = {*reinterpret_cast<const uint32_t *>(seg + 4 * tid),
+                                  *reinterpret_cast<const uint32_t *>(seg + kHalf + 4 * tid)};
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const float xs = (float)(int8_t)(wd[e >> 2] >> (8 * (e & 3)));
             v[e] = fmaf(hc[j][e], xs, v[e]);
           }
         }
-        // z[m] = v[2m] + i v[2m+1], m = 4 tid .. 4 tid + 3, digit-reversed
+        // z[2 tid], z[2 tid + 1] and z[512 + 2 tid], z[513 + 2 tid]: one
+        // 16-byte store each (the pair is swapped where the layout's XOR is odd)
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-          buf[u * kBufElems + padi(digitrev4(4 * tid + e))] = make_float2(v[2 * e], v[2 * e + 1]);
+        for (int h = 0; h < 2; ++h) {
+          const int e0 = 512 * h + 2 * tid;
+          const bool swp = (e0 >> 6) & 1;
+          const float4 pr = swp ? make_float4(v[4 * h + 2], v[4 * h + 3], v[4 * h], v[4 * h + 1])
+                                : make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+          *reinterpret_cast<float4 *>(&buf[u * kBufElems + (swz(e0) & ~1)]) = pr;
+        }
       }
       __syncthreads();
-      // ---- 1024-point FFTs: five radix-4 stages, one butterfly per thread
-      // per spectrum
+      // ---- 1024-point FFTs, 1024 = 16 x 4 x 16 (n = 64 m1 + 16 m2 + n2,
+      // k = l1 + 16 l2 + 64 k2):
+      //   pass 1: A[n2][m2][l1] = W64^(m2 l1) sum_m1 x[64 m1 + 16 m2 + n2] W16^(m1 l1)
+      //   pass 2: B[n2][k1] = W1024^(n2 k1) sum_m2 A[n2][m2][l1] W4^(m2 l2),  k1 = l1 + 16 l2
+      //   pass 3: X[k1 + 64 k2] = sum_n2 B[n2][k1] W16^(n2 k2)
+      // A[n2][m2][l1] and B[n2][l1 + 16 l2] share element l1 + 16 m2 + 64 n2
+      // (m2 <-> l2), and X[k1 + 64 k2] element k1 + 64 n2 (n2 <-> k2), so
+      // passes 2 and 3 read and write the same elements of their thread.
+      {
+        // pass 1: thread t -> spectrum t / 64, (m2, n2) = (t % 64 / 16, t % 16)
+        const int u = tid >> 6, r = tid & 63, m2 = r >> 4, n2 = r & 15;
+        float2 *bu = buf + u * kBufElems;
+        float2 a[16];
+        const bool live = u < nb;
+        if (live) {
 #pragma unroll
-      for (int st = 0; st < 5; ++st) {
-        const int q = 1 << (2 * st);  // quarter span
-        const int L = 4 * q;
-        const int grp = tid / q, p = tid - grp * q;
-        const int i0 = grp * L + p;
-        const int tstep = kHalf / L;  // W_L^p = W_1024^(p tstep)
-        const float2 w1 = __ldg(tw_fft + p * tstep);
-        const float2 w2 = __ldg(tw_fft + 2 * p * tstep);
-        const float2 w3 = __ldg(tw_fft + 3 * p * tstep);
-        float2 y[kBatch][4];
+          for (int m1 = 0; m1 < 16; ++m1) a[m1] = bu[swz(64 * m1 + r)];
+          dft16(a);
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-          const float2 *bu = buf + u * kBufElems;
-          const float2 a0 = bu[padi(i0)];
-          const float2 a1 = cmul(bu[padi(i0 + q)], w1);
-          const float2 a2 = cmul(bu[padi(i0 + 2 * q)], w2);
-          const float2 a3 = cmul(bu[padi(i0 + 3 * q)], w3);
-          const float2 s02 = make_float2(a0.x + a2.x, a0.y + a2.y);
-          const float2 d02 = make_float2(a0.x - a2.x, a0.y - a2.y);
-          const float2 s13 = make_float2(a1.x + a3.x, a1.y + a3.y);
-          const float2 d13 = make_float2(a1.x - a3.x, a1.y - a3.y);
-          y[u][0] = make_float2(s02.x + s13.x, s02.y + s13.y);
-          y[u][1] = make_float2(d02.x + d13.y, d02.y - d13.x);  // a0 - i a1 - a2 + i a3
-          y[u][2] = make_float2(s02.x - s13.x, s02.y - s13.y);
-          y[u][3] = make_float2(d02.x - d13.y, d02.y + d13.x);  // a0 + i a1 - a2 - i a3
+          for (int l1 = 1; l1 < 16; ++l1) a[l1] = cmul(a[l1], __ldg(tw_fft + 16 * m2 * l1));
         }
         __syncthreads();  // every thread has read its inputs
+        if (live) {
+#pragma unroll
+          for (int l1 = 0; l1 < 16; ++l1) bu[swz(l1 + 16 * m2 + 64 * n2)] = a[l1];
+        }
+      }
+      __syncthreads();
+      {
+        // pass 2: thread t -> (n2, l1) = (t / 16, t % 16), every spectrum
+        const int n2 = tid >> 4, l1 = tid & 15;
+        float2 tw[4];
+#pragma unroll
+        for (int l2 = 0; l2 < 4; ++l2) tw[l2] = __ldg(tw_fft + ((n2 * (l1 + 16 * l2)) & (kHalf - 1)));
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
+          if (u >= nb) break;
           float2 *bu = buf + u * kBufElems;
-          bu[padi(i0)] = y[u][0];
-          bu[padi(i0 + q)] = y[u][1];
-          bu[padi(i0 + 2 * q)] = y[u][2];
-          bu[padi(i0 + 3 * q)] = y[u][3];
+          float2 a0 = bu[swz(l1 + 64 * n2)], a1 = bu[swz(l1 + 16 + 64 * n2)];
+          float2 a2 = bu[swz(l1 + 32 + 64 * n2)], a3 = bu[swz(l1 + 48 + 64 * n2)];
+          dft4(a0, a1, a2, a3);
+          bu[swz(l1 + 64 * n2)] = cmul(a0, tw[0]);
+          bu[swz(l1 + 16 + 64 * n2)] = cmul(a1, tw[1]);
+          bu[swz(l1 + 32 + 64 * n2)] = cmul(a2, tw[2]);
+          bu[swz(l1 + 48 + 64 * n2)] = cmul(a3, tw[3]);
         }
-        __syncthreads();
       }
-      // ---- real-FFT split, EQ, requantisation: channels c = 4 tid .. + 3
+      __syncthreads();
+      {
+        // pass 3: thread t -> spectrum t / 64, k1 = t % 64
+        const int u = tid >> 6, k1 = tid & 63;
+        if (u < nb) {
+          float2 *bu = buf + u * kBufElems;
+          float2 a[16];
+#pragma unroll
+          for (int n2 = 0; n2 < 16; ++n2) a[n2] = bu[swz(k1 + 64 * n2)];
+          dft16(a);
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) bu[swz(k1 + 64 * k2)] = a[k2];
+        }
+      }
+      __syncthreads();
+      // ---- real-FFT split, EQ, requantisation: channels c = tid + 256 e
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const int c = 4 * tid + e;
+        const int c = tid + kThreads * e;
         const float2 tw = __ldg(tw_split + c);
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
           if (u >= nb) break;
-          const float2 zc = buf[u * kBufElems + padi(c)];
-          const float2 zr = buf[u * kBufElems + padi((kHalf - c) & (kHalf - 1))];
+          const float2 zc = buf[u * kBufElems + swz(c)];
+          const float2 zr = buf[u * kBufElems + swz((kHalf - c) & (kHalf - 1))];
           // even part (Z[c] + conj Z[N-c]) / 2, odd part (Z[c] - conj Z[N-c]) / (2i)
           const float2 ev = make_float2(0.5f * (zc.x + zr.x), 0.5f * (zc.y - zr.y));
           const float2 od = make_float2(0.5f * (zc.y + zr.y), -0.5f * (zc.x - zr.x));
