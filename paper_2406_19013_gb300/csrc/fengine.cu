@@ -109,18 +109,16 @@ __device__ __forceinline__ int quant(float a) {
 constexpr int kBatch = 4;                         // spectra per inner iteration
 constexpr int kRing = 8;                          // ring slots (>= kTaps - 1 + kBatch)
 constexpr int kRingBytes = kRing * kP;            // 16 KB
-// FFT buffers: element e of a spectrum sits at 64 (e / 64) + ((e % 64) ^
-// (e / 64 % 16)).  The XOR keeps every access pattern of the passes at the
-// two shared-memory wavefronts a warp's float2 access needs: runs of 32
-// consecutive elements (the FIR's stores, the first pass's loads, the last
-// pass, the split) and stride-64 gathers (the first pass's stores and the
-// middle pass) alike; pairs (2k, 2k + 1) stay in one 16-byte slot, swapped
-// when the XOR is odd.
-constexpr int kBufElems = kHalf;
+// FFT buffers: element e of a spectrum sits at e + e / 64 (one pad element
+// per 64).  That keeps the passes' runs of consecutive elements and their
+// stride-64 gathers at the two shared-memory wavefronts a warp's float2
+// access needs, and every unrolled access of a pass is its thread's base
+// plus a constant offset.
+constexpr int kBufElems = kHalf + kHalf / 64;
 constexpr int kBufBytes = kBatch * kBufElems * 8;
 constexpr int kStageBytes = kHalf * kSpecTile;    // 32 KB, [spectrum][channel]
 
-__device__ __forceinline__ int swz(int e) { return (e & ~63) | ((e & 63) ^ ((e >> 6) & 15)); }
+__device__ __forceinline__ int swz(int e) { return e + (e >> 6); }
 static_assert(kSpecTile % kBatch == 0, "tile of whole batches");
 static_assert(kRing >= kTaps - 1 + kBatch && (kRing & (kRing - 1)) == 0, "ring size");
 
@@ -137,6 +135,10 @@ __global__ void __launch_bounds__(kThreads, 2)
   float2 *buf = reinterpret_cast<float2 *>(fe_smem + kRingBytes);  // [kBatch][kBufElems]
   uint8_t *stage = fe_smem + kRingBytes + kBufBytes;               // [kSpecTile][kHalf]
   const int tid = threadIdx.x;
+  // W64^j = W1024^(16 j), the first pass's twiddles, kept in shared memory
+  __shared__ float2 tw64[64];
+  if (tid < 64) tw64[tid] = __ldg(tw_fft + 16 * tid);
+  __syncthreads();
   const int n_tiles = (n_spec + kSpecTile - 1) / kSpecTile;
   const long long stream_len = (long long)(n_spec + kTaps - 1) * kP;
 
@@ -145,9 +147,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int k0 = tile * kSpecTile;
     const int ns = min(kSpecTile, n_spec - k0);
     const int8_t *x = adc + (long long)in * stream_len;
-    float g[4];  // EQ gains of this thread's channels tid + 256 e
-#pragma unroll
-    for (int e = 0; e < 4; ++e) g[e] = __ldg(eq + (long long)in * kHalf + tid + kThreads * e);
     // prime the ring with segments k0 .. k0 + 2
     for (int j = 0; j < kTaps - 1; ++j)
       *reinterpret_cast<uint2 *>(&ring[((k0 + j) & (kRing - 1)) * kP + 8 * tid]) =
@@ -163,22 +162,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       __syncthreads();
       // ---- polyphase FIR of each spectrum of the batch.  The filter
       // coefficients of this thread's 8 samples (4 tid .. + 3 and 1024 + 4 tid
-      // .. + 3 of the 2048), all four taps, are re-read (from L1) per batch,
-      // so that they do not stay live through the FFT passes.
-      float hc[kTaps][8];
-#pragma unroll
-      for (int j = 0; j < kTaps; ++j)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const float4 c4 = __ldg(reinterpret_cast<const float4 *>(proto + j * kP + h * kHalf + 4 * tid));
-          hc[j][4 * h] = c4.x;
-          hc[j][4 * h + 1] = c4.y;
-          hc[j][4 * h + 2] = c4.z;
-          hc[j][4 * h + 3] = c4.w;
-        }
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        if (u >= nb) break;
+      // .. + 3 of the 2048) are read from L1 per tap, so that they do not stay
+      // live through the FFT passes.
+#pragma unroll 1
+      for (int u = 0; u < nb; ++u) {
         const int k = k0 + s0 + u;
         float v[8];
 #pragma unroll
@@ -186,23 +173,28 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int j = 0; j < kTaps; ++j) {
           const int8_t *seg = &ring[((k + j) & (kRing - 1)) * kP];
-          const uint32_t wd[2] = {*reinterpret_cast<const uint32_t *>(seg + 4 * tid),
-                                  *reinterpret_cast<const uint32_t *>(seg + kHalf + 4 * tid)};
+          const float4 h0 = __ldg(reinterpret_cast<const float4 *>(proto + j * kP + 4 * tid));
+          const float4 h1 = __ldg(reinterpret_cast<const float4 *>(proto + j * kP + kHalf + 4 * tid));
+          const float hc[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+          // int8 -> fp32 without a conversion instruction: with the sign bit
+          // flipped, byte b + 128 placed under the exponent of 2^23 is the
+          // float 2^23 + b + 128, and subtracting 2^23 + 128 is exact
+          const uint32_t wd[2] = {*reinterpret_cast<const uint32_t *>(seg + 4 * tid) ^ 0x80808080u,
+                                  *reinterpret_cast<const uint32_t *>(seg + kHalf + 4 * tid) ^
+                                      0x80808080u};
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            const float xs = (float)(int8_t)(wd[e >> 2] >> (8 * (e & 3)));
-            v[e] = fmaf(hc[j][e], xs, v[e]);
+            const uint32_t f = __byte_perm(wd[e >> 2], 0x4B000000u, 0x7650 + (e & 3));
+            const float xs = __uint_as_float(f) - 8388736.0f;
+            v[e] = fmaf(hc[e], xs, v[e]);
           }
         }
-        // z[2 tid], z[2 tid + 1] and z[512 + 2 tid], z[513 + 2 tid]: one
-        // 16-byte store each (the pair is swapped where the layout's XOR is odd)
+        // z[2 tid], z[2 tid + 1] and z[512 + 2 tid], z[513 + 2 tid]
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int e0 = 512 * h + 2 * tid;
-          const bool swp = (e0 >> 6) & 1;
-          const float4 pr = swp ? make_float4(v[4 * h + 2], v[4 * h + 3], v[4 * h], v[4 * h + 1])
-                                : make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
-          *reinterpret_cast<float4 *>(&buf[u * kBufElems + (swz(e0) & ~1)]) = pr;
+          float2 *d = &buf[u * kBufElems + swz(512 * h + 2 * tid)];
+          d[0] = make_float2(v[4 * h], v[4 * h + 1]);
+          d[1] = make_float2(v[4 * h + 2], v[4 * h + 3]);
         }
       }
       __syncthreads();
@@ -225,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           for (int m1 = 0; m1 < 16; ++m1) a[m1] = bu[swz(64 * m1 + r)];
           dft16(a);
 #pragma unroll
-          for (int l1 = 1; l1 < 16; ++l1) a[l1] = cmul(a[l1], __ldg(tw_fft + 16 * m2 * l1));
+          for (int l1 = 1; l1 < 16; ++l1) a[l1] = cmul(a[l1], tw64[m2 * l1]);
         }
         __syncthreads();  // every thread has read its inputs
         if (live) {
@@ -269,10 +261,11 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       __syncthreads();
       // ---- real-FFT split, EQ, requantisation: channels c = tid + 256 e
-#pragma unroll
+#pragma unroll 1
       for (int e = 0; e < 4; ++e) {
         const int c = tid + kThreads * e;
         const float2 tw = __ldg(tw_split + c);
+        const float g = __ldg(eq + (long long)in * kHalf + c);  // EQ gain
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
           if (u >= nb) break;
@@ -282,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           const float2 ev = make_float2(0.5f * (zc.x + zr.x), 0.5f * (zc.y - zr.y));
           const float2 od = make_float2(0.5f * (zc.y + zr.y), -0.5f * (zc.x - zr.x));
           const float2 t = cmul(tw, od);
-          const float2 gX = make_float2(g[e] * (ev.x + t.x), g[e] * (ev.y + t.y));
+          const float2 gX = make_float2(g * (ev.x + t.x), g * (ev.y + t.y));
           if (kQuant) {
             const int qr = quant(gX.x), qi = quant(gX.y);
             stage[(s0 + u) * kHalf + c] = (uint8_t)(((qr & 15) << 4) | (qi & 15));
