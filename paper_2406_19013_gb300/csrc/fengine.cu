@@ -21,8 +21,9 @@
 //     segments of overlap at the tile start);
 //   - spectra go through in batches of kBatch, so that every barrier of the
 //     FFT is shared by kBatch independent butterflies per thread;
-//   - thread t filters samples 4 t .. 4 t + 3 and 1024 + 4 t .. + 3, holding
-//     its 32 filter coefficients in registers, and pairs them as
+//   - thread t filters samples 4 t .. 4 t + 3 and 1024 + 4 t .. + 3 (filter
+//     coefficients read from L1 per tap, int8 samples turned into fp32 with a
+//     byte permute and an exact subtraction), and pairs them as
 //     z[m] = v[2m] + i v[2m+1];
 //   - a 1024-point complex FFT runs in three in-place passes over shared
 //     memory, 1024 = 16 x 4 x 16 (each thread does a 16-point FFT in registers
@@ -118,7 +119,7 @@ constexpr int kBufElems = kHalf + kHalf / 64;
 constexpr int kBufBytes = kBatch * kBufElems * 8;
 constexpr int kStageBytes = kHalf * kSpecTile;    // 32 KB, [spectrum][channel]
 
-__device__ __forceinline__ int swz(int e) { return e + (e >> 6); }
+__device__ __forceinline__ int bpos(int e) { return e + (e >> 6); }
 static_assert(kSpecTile % kBatch == 0, "tile of whole batches");
 static_assert(kRing >= kTaps - 1 + kBatch && (kRing & (kRing - 1)) == 0, "ring size");
 
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         // z[2 tid], z[2 tid + 1] and z[512 + 2 tid], z[513 + 2 tid]
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          float2 *d = &buf[u * kBufElems + swz(512 * h + 2 * tid)];
+          float2 *d = &buf[u * kBufElems + bpos(512 * h + 2 * tid)];
           d[0] = make_float2(v[4 * h], v[4 * h + 1]);
           d[1] = make_float2(v[4 * h + 2], v[4 * h + 3]);
         }
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const bool live = u < nb;
         if (live) {
 #pragma unroll
-          for (int m1 = 0; m1 < 16; ++m1) a[m1] = bu[swz(64 * m1 + r)];
+          for (int m1 = 0; m1 < 16; ++m1) a[m1] = bu[bpos(64 * m1 + r)];
           dft16(a);
 #pragma unroll
           for (int l1 = 1; l1 < 16; ++l1) a[l1] = cmul(a[l1], tw64[m2 * l1]);
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         __syncthreads();  // every thread has read its inputs
         if (live) {
 #pragma unroll
-          for (int l1 = 0; l1 < 16; ++l1) bu[swz(l1 + 16 * m2 + 64 * n2)] = a[l1];
+          for (int l1 = 0; l1 < 16; ++l1) bu[bpos(l1 + 16 * m2 + 64 * n2)] = a[l1];
         }
       }
       __syncthreads();
@@ -236,13 +237,13 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int u = 0; u < kBatch; ++u) {
           if (u >= nb) break;
           float2 *bu = buf + u * kBufElems;
-          float2 a0 = bu[swz(l1 + 64 * n2)], a1 = bu[swz(l1 + 16 + 64 * n2)];
-          float2 a2 = bu[swz(l1 + 32 + 64 * n2)], a3 = bu[swz(l1 + 48 + 64 * n2)];
+          float2 a0 = bu[bpos(l1 + 64 * n2)], a1 = bu[bpos(l1 + 16 + 64 * n2)];
+          float2 a2 = bu[bpos(l1 + 32 + 64 * n2)], a3 = bu[bpos(l1 + 48 + 64 * n2)];
           dft4(a0, a1, a2, a3);
-          bu[swz(l1 + 64 * n2)] = cmul(a0, tw[0]);
-          bu[swz(l1 + 16 + 64 * n2)] = cmul(a1, tw[1]);
-          bu[swz(l1 + 32 + 64 * n2)] = cmul(a2, tw[2]);
-          bu[swz(l1 + 48 + 64 * n2)] = cmul(a3, tw[3]);
+          bu[bpos(l1 + 64 * n2)] = cmul(a0, tw[0]);
+          bu[bpos(l1 + 16 + 64 * n2)] = cmul(a1, tw[1]);
+          bu[bpos(l1 + 32 + 64 * n2)] = cmul(a2, tw[2]);
+          bu[bpos(l1 + 48 + 64 * n2)] = cmul(a3, tw[3]);
         }
       }
       __syncthreads();
@@ -253,10 +254,10 @@ __global__ void __launch_bounds__(kThreads, 2)
           float2 *bu = buf + u * kBufElems;
           float2 a[16];
 #pragma unroll
-          for (int n2 = 0; n2 < 16; ++n2) a[n2] = bu[swz(k1 + 64 * n2)];
+          for (int n2 = 0; n2 < 16; ++n2) a[n2] = bu[bpos(k1 + 64 * n2)];
           dft16(a);
 #pragma unroll
-          for (int k2 = 0; k2 < 16; ++k2) bu[swz(k1 + 64 * k2)] = a[k2];
+          for (int k2 = 0; k2 < 16; ++k2) bu[bpos(k1 + 64 * k2)] = a[k2];
         }
       }
       __syncthreads();
@@ -269,8 +270,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
           if (u >= nb) break;
-          const float2 zc = buf[u * kBufElems + swz(c)];
-          const float2 zr = buf[u * kBufElems + swz((kHalf - c) & (kHalf - 1))];
+          const float2 zc = buf[u * kBufElems + bpos(c)];
+          const float2 zr = buf[u * kBufElems + bpos((kHalf - c) & (kHalf - 1))];
           // even part (Z[c] + conj Z[N-c]) / 2, odd part (Z[c] - conj Z[N-c]) / (2i)
           const float2 ev = make_float2(0.5f * (zc.x + zr.x), 0.5f * (zc.y - zr.y));
           const float2 od = make_float2(0.5f * (zc.y + zr.y), -0.5f * (zc.x - zr.x));
