@@ -59,11 +59,14 @@ extern "C" {
 #define CORR_ETIMEOUT (-5) /* a device-side wait ran out; results are void */
 #define CORR_ESTATE (-6)   /* call not valid in the context's current state */
 
-/* Largest block_len accepted.  Each block is accumulated in fp32 inside the
- * tensor-core accumulator before it is folded into int64; a block of L samples
- * bounds every partial sum by 128 * L, which stays an exactly representable
- * integer (< 2^24) for L <= 131071. */
-#define CORR_MAX_BLOCK_LEN 131071
+/* Largest block_len accepted (Sec. 2.4's integrations are blocks of many
+ * samples; 2^24 - 1 bounds the host-side sample counters of one block). */
+#define CORR_MAX_BLOCK_LEN 16777215
+/* Samples the tensor cores accumulate in fp32 before a fold into int64.  A
+ * partial over L samples is bounded by 128 * L, an exactly representable
+ * integer (< 2^24) for L <= 131071; longer blocks, and launches of several
+ * blocks, are folded at least this often. */
+#define CORR_FOLD_SAMPLES 131071
 /* Largest input count N = n_ant * n_pol accepted. */
 #define CORR_MAX_INPUTS 8192
 
@@ -97,7 +100,8 @@ int corr_push_block(corr_ctx *ctx, const uint8_t *d_block, void *stream);
  * Integrates n_blocks blocks (d_blocks: host array of n_blocks device
  * pointers, each as for corr_push_block).  Equivalent to n_blocks calls of
  * corr_push_block, but up to 8 blocks share one launch and one fold into the
- * int64 buffer (fewer while 8 * block_len exceeds CORR_MAX_BLOCK_LEN).  The
+ * int64 buffer (fewer while 8 * block_len exceeds CORR_FOLD_SAMPLES; a block
+ * longer than that is folded every CORR_FOLD_SAMPLES samples or fewer).  The
  * pointer array itself may be reused as soon as the call returns.
  * Errors: CORR_EINVAL (NULL ctx or array, n_blocks < 1, a NULL or misaligned
  * block pointer; nothing is enqueued), CORR_ECUDA.
@@ -180,7 +184,9 @@ int corr_plan_cover(int n_in, int cover, uint8_t *cover_out, int *n_units,
  *   - Units are cut at 128-sample stage boundaries into items, and every CTA
  *     (at most `grid`) runs a contiguous run of items of about equal
  *     modelled cost.  That cost is the operand rows unpacked plus a fixed
- *     fold cost per item.
+ *     fold cost per item.  No item spans more than CORR_FOLD_SAMPLES / 128
+ *     stages (1023): each item folds its fp32 partials into int64 once.
+ *   - n_blocks: 1..8 (the blocks of one launch).
  *   - items, if not NULL, receives up to `cap` rows of 5 ints:
  *     (problem = 0, template, channel, first stage, stages).  Stage k of the
  *     launch is 128-sample stage k % ceil(block_len / 128) of block
@@ -209,10 +215,20 @@ int corr_plan_items(int n_in, int n_chan, int block_len, int n_blocks, int cover
  * loads the library holds until the process exits; the call allocates nothing
  * on the device or the host.
  *   - Limits: n_ant * n_pol <= CORR_STATIC_MAX_INPUTS, block_len a multiple of
- *     16 (at most CORR_MAX_BLOCK_LEN); d_block and d_vis 16-byte aligned.
+ *     16 (at most CORR_STATIC_MAX_BLOCK_LEN, one fold per call); d_block and
+ *     d_vis 16-byte aligned.
  *     Anything else returns CORR_EINVAL before any work is enqueued.
  *   - The first call on a device looks up the array's device address and the
- *     device limits; make that first call before any stream capture.
+ *     device limits; make that first call before any stream capture.  With
+ *     CUDA's default lazy module loading, that first lookup (or the first
+ *     launch) also loads the library's device code on that device, which the
+ *     driver allocates once, outside any framework's pool: make the first
+ *     call at set-up, not on the path that must not allocate.  Later calls
+ *     allocate nothing.
+ *   - Each call enqueues a one-block set-up kernel that receives the tile
+ *     schedule by value in its parameters and writes it into the array
+ *     (nothing is copied from host memory), a memset of d_vis and the
+ *     X-engine launch.
  *   - Every call shares the one array and leaves its contents behind: calls
  *     whose work overlaps on the GPU (other streams, other host threads) race
  *     on it; serialise them.
@@ -224,6 +240,7 @@ int corr_plan_items(int n_in, int n_chan, int block_len, int n_blocks, int cover
  */
 #define CORR_STATIC_SCRATCH_BYTES 4096
 #define CORR_STATIC_MAX_INPUTS 256
+#define CORR_STATIC_MAX_BLOCK_LEN 131056
 int corr_xcorr_static(const uint8_t *d_block, int n_ant, int n_pol, int n_chan, int block_len,
                       int64_t *d_vis, void *stream);
 
@@ -467,6 +484,27 @@ int corr_fengine_run(corr_fengine *f, const int8_t *d_adc, uint8_t *d_out, void 
 int corr_fengine_spectra(corr_fengine *f, const int8_t *d_adc, float *d_spec, void *stream);
 
 void corr_fengine_destroy(corr_fengine *f);
+
+/*
+ * Dense tensor-core rate of the current GPU (a measurement helper for the
+ * roofline of the CMAC kernel; the paper has no counterpart).  Launches one
+ * CTA per SM; in each, `issuers` threads (1..4) issue `iters` x 4
+ * back-to-back tcgen05.mma.kind::f8f6f4 instructions (E5M2 operands, fp32
+ * accumulation, M = 128, N = n, K = 32) into their own TMEM accumulators,
+ * with both operands in 128B-swizzled shared memory, or with A in TMEM when
+ * a_from_tmem is 1.  The work is
+ *     n_SM * issuers * iters * 4 * 2 * 128 * n * 32   floating-point ops;
+ * the caller times the launch on `stream` (CUDA events).
+ *   - n: multiple of 16 in [16, 256]; issuers * n (+ 32 with a_from_tmem)
+ *     <= 512 TMEM columns; iters in [1, 10^7].
+ *   - d_status: device int; bit 0 is set if the final wait for the MMAs ran
+ *     out (2 s).  d_cycles: device int64[n_SM] or NULL; receives each CTA's
+ *     clock64 cycles from its first MMA to the completion of its last.
+ * Stream-ordered and asynchronous.  Errors: CORR_EINVAL, CORR_EARCH,
+ * CORR_ECUDA.
+ */
+int corr_mma_rate(int n, int issuers, int iters, int a_from_tmem, int *d_status,
+                  long long *d_cycles, void *stream);
 
 /* Static string naming a CORR_* code. */
 const char *corr_strerror(int code);

@@ -24,7 +24,9 @@ CORR_ECUDA = -3
 CORR_EARCH = -4
 CORR_ETIMEOUT = -5
 CORR_ESTATE = -6
-CORR_MAX_BLOCK_LEN = 131071
+CORR_MAX_BLOCK_LEN = 16777215
+CORR_FOLD_SAMPLES = 131071
+CORR_STATIC_MAX_BLOCK_LEN = 131056
 CORR_MAX_INPUTS = 8192
 CORR_COVER_WINDOW = 0
 CORR_COVER_STRIPS = 1
@@ -62,6 +64,7 @@ ABI = [
     ("corr_push_block_tcn", _ci, [_vp, _vp, _vp]),
     ("corr_selftest_timeout", _ci, [_vp, _vp, _ci, _vp]),
     ("corr_xcorr_static", _ci, [_vp, _ci, _ci, _ci, _ci, _vp, _vp]),
+    ("corr_mma_rate", _ci, [_ci, _ci, _ci, _ci, _vp, _vp, _vp]),
     ("corr_launch_count", _ll, [_vp]),
     ("corr_destroy", None, [_vp]),
     ("corr_strerror", ctypes.c_char_p, [_ci]),
@@ -222,6 +225,37 @@ def xcorr_static(block, n_ant: int, n_pol: int, vis=None, stream=None):
     _ck(load().corr_xcorr_static(block.data_ptr(), n_ant, n_pol, n_chan, block_len, vis.data_ptr(),
                                  _stream_handle(stream)), "corr_xcorr_static")
     return vis
+
+
+def mma_rate(n: int = 256, issuers: int = 1, iters: int = 10000, a_from_tmem: bool = False,
+             reps: int = 3, stream=None):
+    """Dense E5M2 tcgen05 MMA rate (corr_mma_rate), best of `reps` launches
+    timed with CUDA events: returns (TFLOP/s, ms per launch, median cycles per
+    MMA per issuing thread)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    cycles = torch.zeros(n_sm, dtype=torch.int64, device=dev)
+    st = torch.cuda.current_stream() if stream is None else stream
+    h = _stream_handle(st)
+    lib = load()
+    best_ms, best_cyc = None, None
+    for _ in range(max(1, reps) + 1):  # the first launch is a warm-up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        _ck(lib.corr_mma_rate(n, issuers, iters, int(a_from_tmem), status.data_ptr(),
+                              cycles.data_ptr(), h), "corr_mma_rate")
+        b.record(st)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        if int(status.item()) != 0:
+            raise CorrError(CORR_ETIMEOUT, "corr_mma_rate")
+        cyc = float(cycles.float().median().item()) / (4 * iters)
+        if best_ms is None or ms < best_ms:
+            best_ms, best_cyc = ms, cyc
+    flop = n_sm * issuers * iters * 4 * 2 * 128 * n * 32
+    return flop / (best_ms / 1e3) / 1e12, best_ms, best_cyc
 
 
 def n_pairs(n_in: int) -> int:

@@ -167,8 +167,10 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
   ctx->z_stage_bytes = L.z_stage_bytes;
   ctx->pk_stage_bytes = L.pk_stage_bytes;
   ctx->smem_bytes = L.smem_bytes;
-  // a fold must come before 2^24 / 128 samples have been accumulated in fp32
-  ctx->per_launch = std::max(1, std::min(xe::kMaxBlocksPerLaunch, CORR_MAX_BLOCK_LEN / block_len));
+  // a fold must come before 2^24 / 128 samples have been accumulated in
+  // fp32: launches of several blocks stay within that window, and the item
+  // split cuts a longer block into pieces that each fold on their own
+  ctx->per_launch = std::max(1, std::min(xe::kMaxBlocksPerLaunch, CORR_FOLD_SAMPLES / block_len));
   if (ctx->pitch != block_len) ctx->per_launch = 1;  // one pitched staging buffer
 
   int rc = CORR_OK;
@@ -453,8 +455,8 @@ int corr_plan(int n_in, uint8_t *cover, int *n_units, long long *issued_cmacs) {
 int corr_plan_items(int n_in, int n_chan, int block_len, int n_blocks, int cover, int grid,
                     int *items, int cap, int *n_items, int *cta_first, int *used_grid) {
   if (n_in <= 0 || n_in > CORR_MAX_INPUTS || n_chan <= 0 || block_len <= 0 ||
-      block_len > CORR_MAX_BLOCK_LEN || n_blocks <= 0 || grid <= 0 || cover < 0 || cover > 2 ||
-      (long long)n_blocks * block_len > CORR_MAX_BLOCK_LEN)
+      block_len > CORR_MAX_BLOCK_LEN || n_blocks <= 0 || n_blocks > xe::kMaxBlocksPerLaunch ||
+      grid <= 0 || cover < 0 || cover > 2)
     return CORR_EINVAL;
   const std::vector<XUnit> units = xe::build_schedule(n_in, cover);
   if (units.empty()) return CORR_EINVAL;

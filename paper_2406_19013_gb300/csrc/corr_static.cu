@@ -41,6 +41,33 @@ std::mutex g_setup_mutex;
 unsigned char *g_scratch_addr[kMaxDevices];  // device address of the array, per device
 int g_smem_optin[kMaxDevices];
 int g_n_sm[kMaxDevices];
+unsigned long long g_timeout_ns = 2000000000ull;  // device-side wait limit (CORR_TIMEOUT_MS)
+
+// The schedule and problem descriptor of one call, passed by value in the
+// parameters of the set-up kernel below (so nothing is copied from host
+// memory, which a captured copy would read again at replay).
+constexpr int kMaxCallUnits = 4;
+struct StaticPlan {
+  xe::XProb prob;
+  xe::XUnit units[kMaxCallUnits];
+  int n_units;
+};
+
+// Writes the call's problem descriptor and schedule into the scratch array
+// and clears the status word.  One block; the X-engine launch that follows on
+// the same stream reads them.
+__global__ void static_setup_kernel(const __grid_constant__ StaticPlan plan, xe::XProb *d_prob,
+                                    xe::XUnit *d_units, int *d_status) {
+  static_assert(sizeof(xe::XUnit) % 4 == 0 && sizeof(xe::XProb) % 4 == 0, "word copies");
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(plan.units);
+  uint32_t *dst = reinterpret_cast<uint32_t *>(d_units);
+  const int n_words = plan.n_units * (int)(sizeof(xe::XUnit) / 4);
+  for (int k = threadIdx.x; k < n_words; k += blockDim.x) dst[k] = src[k];
+  const uint32_t *ps = reinterpret_cast<const uint32_t *>(&plan.prob);
+  uint32_t *pd = reinterpret_cast<uint32_t *>(d_prob);
+  for (int k = threadIdx.x; k < (int)(sizeof(xe::XProb) / 4); k += blockDim.x) pd[k] = ps[k];
+  if (threadIdx.x == 0) *d_status = 0;
+}
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
@@ -73,6 +100,10 @@ int setup_device(int dev) {
   }
   void *addr = nullptr;
   if (cudaGetSymbolAddress(&addr, g_static_scratch) != cudaSuccess || !addr) return CORR_ECUDA;
+  if (const char *env = std::getenv("CORR_TIMEOUT_MS")) {
+    const long long ms = std::atoll(env);
+    if (ms > 0) g_timeout_ns = (unsigned long long)ms * 1000000ull;
+  }
   g_smem_optin[dev] = optin;
   g_n_sm[dev] = prop.multiProcessorCount;
   g_scratch_addr[dev] = static_cast<unsigned char *>(addr);
@@ -137,7 +168,7 @@ extern "C" int corr_xcorr_static(const uint8_t *d_block, int n_ant, int n_pol, i
       (n_pol != 1 && n_pol != 2))
     return CORR_EINVAL;
   const long long N = (long long)n_ant * n_pol;
-  if (N > CORR_STATIC_MAX_INPUTS || block_len > CORR_MAX_BLOCK_LEN || block_len % 16 != 0)
+  if (N > CORR_STATIC_MAX_INPUTS || block_len > CORR_STATIC_MAX_BLOCK_LEN || block_len % 16 != 0)
     return CORR_EINVAL;
   if ((reinterpret_cast<uintptr_t>(d_block) & 15u) || (reinterpret_cast<uintptr_t>(d_vis) & 15u))
     return CORR_EINVAL;
@@ -147,9 +178,12 @@ extern "C" int corr_xcorr_static(const uint8_t *d_block, int n_ant, int n_pol, i
   int rc = setup_device(dev);
   if (rc != CORR_OK) return rc;
 
-  xe::XUnit units[4];
+  StaticPlan plan;
+  std::memset(&plan, 0, sizeof(plan));
+  xe::XUnit *units = plan.units;
   const int n_tpl = plan_single_window((int)N, units);
-  if (n_tpl > kMaxStaticUnits) return CORR_EINVAL;
+  if (n_tpl > kMaxStaticUnits || n_tpl > kMaxCallUnits) return CORR_EINVAL;
+  plan.n_units = n_tpl;
   int max_z = 0, max_pk = 0;
   for (int k = 0; k < n_tpl; ++k) {
     max_z = std::max(max_z, units[k].z_rows);
@@ -176,8 +210,7 @@ extern "C" int corr_xcorr_static(const uint8_t *d_block, int n_ant, int n_pol, i
   xe::XProb *d_prob = reinterpret_cast<xe::XProb *>(scratch + kStatusBytes);
   xe::XUnit *d_units = reinterpret_cast<xe::XUnit *>(scratch + kStatusBytes + kProbBytes);
   const size_t vis_bytes = (size_t)n_chan * (size_t)(N * (N + 1) / 2) * 16;
-  xe::XProb prob;
-  std::memset(&prob, 0, sizeof(prob));
+  xe::XProb &prob = plan.prob;
   prob.units = d_units;
   prob.acc = d_vis;
   prob.n_pairs = N * (N + 1) / 2;
@@ -186,16 +219,13 @@ extern "C" int corr_xcorr_static(const uint8_t *d_block, int n_ant, int n_pol, i
   prob.pk_per_block = (block_len + xe::kPkSamples - 1) / xe::kPkSamples;
   prob.map0 = 0;
   // the scratch keeps the previous call's contents: rewrite the schedule and
-  // the problem, and clear the status word; the visibilities accumulate from
-  // zero.  The host copies are pageable, so each returns once its bytes are
-  // staged and the locals may go out of scope.
-  if ((rc = rc_of(cudaMemcpyAsync(d_units, units, n_tpl * sizeof(xe::XUnit), cudaMemcpyHostToDevice,
-                                  st))) != CORR_OK ||
-      (rc = rc_of(cudaMemcpyAsync(d_prob, &prob, sizeof(prob), cudaMemcpyHostToDevice, st))) !=
-          CORR_OK ||
-      (rc = rc_of(cudaMemsetAsync(d_status, 0, sizeof(int), st))) != CORR_OK ||
-      (rc = rc_of(cudaMemsetAsync(d_vis, 0, vis_bytes, st))) != CORR_OK ||
-      (rc = rc_of(xe::cmac_set_smem(optin))) != CORR_OK)
+  // the problem and clear the status word (a set-up kernel that receives
+  // them by value), and start the visibilities, which the X-engine
+  // accumulates into, from zero
+  if ((rc = rc_of(xe::cmac_set_smem(optin))) != CORR_OK) return rc;
+  static_setup_kernel<<<1, 128, 0, st>>>(plan, d_prob, d_units, d_status);
+  if ((rc = rc_of(cudaGetLastError())) != CORR_OK ||
+      (rc = rc_of(cudaMemsetAsync(d_vis, 0, vis_bytes, st))) != CORR_OK)
     return rc;
 
   xe::XMaps maps;
@@ -219,7 +249,7 @@ extern "C" int corr_xcorr_static(const uint8_t *d_block, int n_ant, int n_pol, i
   p.implicit_n_chan = n_chan;
   p.implicit_npk = prob.pk_per_block;
   p.status = d_status;
-  p.timeout_ns = 2000000000ull;
+  p.timeout_ns = g_timeout_ns;
   p.z_stages = z_stages;
   p.pk_stages = pk_stages;
   p.z_stage_bytes = (uint32_t)z_bytes;

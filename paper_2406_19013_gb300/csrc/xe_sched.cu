@@ -180,7 +180,7 @@ bool stage_layout(const std::vector<const std::vector<XUnit> *> &unit_sets, int 
 }
 
 int build_items(const std::vector<ProbWork> &probs, int grid, std::vector<XItem> &items,
-                std::vector<int> &cta_first, int min_split_pk) {
+                std::vector<int> &cta_first, int min_split_pk, int max_item_pk) {
   items.clear();
   cta_first.clear();
   // Cost model, in operand-row chunks: unpacking one 64-sample chunk of one
@@ -188,8 +188,9 @@ int build_items(const std::vector<ProbWork> &probs, int grid, std::vector<XItem>
   // column (its int64 atomic adds and the TMEM drain).
   constexpr long long kFold = 16;
   struct PW {
-    int cpb, ppb, npk;
+    int cpb, ppb, npk, nseg;  // nseg: fold-window segments of a unit's stages
   };
+  if (max_item_pk < 1) max_item_pk = 1;
   std::vector<PW> pw(probs.size());
   long long total = 0;
   for (size_t p = 0; p < probs.size(); ++p) {
@@ -197,9 +198,10 @@ int build_items(const std::vector<ProbWork> &probs, int grid, std::vector<XItem>
     pw[p].cpb = (pr.block_len + kChunkSamples - 1) / kChunkSamples;
     pw[p].ppb = (pr.block_len + kPkSamples - 1) / kPkSamples;
     pw[p].npk = pw[p].ppb * pr.n_blocks;
+    pw[p].nseg = (pw[p].npk + max_item_pk - 1) / max_item_pk;
     for (const XUnit &u : *pr.units)
       total += (long long)pr.n_chan *
-               ((long long)pw[p].cpb * pr.n_blocks * u.z_rows + kFold * u.work);
+               ((long long)pw[p].cpb * pr.n_blocks * u.z_rows + kFold * u.work * pw[p].nseg);
   }
   if (total == 0 || grid <= 0) {
     cta_first.push_back(0);
@@ -225,58 +227,61 @@ int build_items(const std::vector<ProbWork> &probs, int grid, std::vector<XItem>
     cta_first.push_back((int)items.size());
     if (cta < grid) target = (remaining + (grid - cta) - 1) / (grid - cta);
   };
-  for (size_t p = 0; p < probs.size(); ++p) {
-    const ProbWork &pr = probs[p];
-    for (int t = 0; t < (int)pr.units->size(); ++t) {
-      const XUnit &u = (*pr.units)[t];
-      const long long fold = kFold * u.work;
-      for (int c = 0; c < pr.n_chan; ++c) {
-        int pk = 0;
-        const int npk = pw[p].npk;
-        while (pk < npk) {
-          if (cta == grid - 1) {  // the last CTA takes everything left
-            const long long cost = range_cost(p, pk, npk, u.z_rows) + fold;
-            items.push_back({(int)p, t, c, pk, npk - pk});
-            load += cost;
-            pk = npk;
-            continue;
-          }
-          const long long rest = range_cost(p, pk, npk, u.z_rows) + fold;
-          if (load + rest <= target) {
-            items.push_back({(int)p, t, c, pk, npk - pk});
-            load += rest;
-            pk = npk;
-            if (load >= target) close_cta();
-            continue;
-          }
-          // the rest overflows this CTA: take the stages that fit, if that
-          // leaves pieces of at least min_split_pk stages on both sides
-          int n = 0;
-          const long long room = target - load - fold;
-          if (room > 0) {
-            const long long per = (long long)kChunksPerPk * u.z_rows;
-            n = (int)std::min<long long>(npk - pk, room / per);
-            while (n > 0 && range_cost(p, pk, pk + n, u.z_rows) > room) --n;
-          }
-          if (n >= min_split_pk && npk - pk - n >= min_split_pk) {
-            items.push_back({(int)p, t, c, pk, n});
-            load += range_cost(p, pk, pk + n, u.z_rows) + fold;
-            remaining += fold;  // the rest of the unit is folded once more
-            pk += n;
-            close_cta();
-          } else if (load == 0 || 2 * (load + rest - target) < rest) {
-            // no useful split: the whole rest goes here when this CTA is
-            // empty or when most of the rest fits
-            items.push_back({(int)p, t, c, pk, npk - pk});
-            load += rest;
-            pk = npk;
-            close_cta();
-          } else {
-            close_cta();
-          }
-        }
+  // deals the stages [pk, npk) of unit (p, t, c) over the CTAs
+  auto deal = [&](size_t p, int t, int c, int pk, int npk) {
+    const XUnit &u = (*probs[p].units)[t];
+    const long long fold = kFold * u.work;
+    while (pk < npk) {
+      if (cta == grid - 1) {  // the last CTA takes everything left
+        const long long cost = range_cost(p, pk, npk, u.z_rows) + fold;
+        items.push_back({(int)p, t, c, pk, npk - pk});
+        load += cost;
+        pk = npk;
+        continue;
+      }
+      const long long rest = range_cost(p, pk, npk, u.z_rows) + fold;
+      if (load + rest <= target) {
+        items.push_back({(int)p, t, c, pk, npk - pk});
+        load += rest;
+        pk = npk;
+        if (load >= target) close_cta();
+        continue;
+      }
+      // the rest overflows this CTA: take the stages that fit, if that
+      // leaves pieces of at least min_split_pk stages on both sides
+      int n = 0;
+      const long long room = target - load - fold;
+      if (room > 0) {
+        const long long per = (long long)kChunksPerPk * u.z_rows;
+        n = (int)std::min<long long>(npk - pk, room / per);
+        while (n > 0 && range_cost(p, pk, pk + n, u.z_rows) > room) --n;
+      }
+      if (n >= min_split_pk && npk - pk - n >= min_split_pk) {
+        items.push_back({(int)p, t, c, pk, n});
+        load += range_cost(p, pk, pk + n, u.z_rows) + fold;
+        remaining += fold;  // the rest of the unit is folded once more
+        pk += n;
+        close_cta();
+      } else if (load == 0 || 2 * (load + rest - target) < rest) {
+        // no useful split: the whole rest goes here when this CTA is
+        // empty or when most of the rest fits
+        items.push_back({(int)p, t, c, pk, npk - pk});
+        load += rest;
+        pk = npk;
+        close_cta();
+      } else {
+        close_cta();
       }
     }
+  };
+  for (size_t p = 0; p < probs.size(); ++p) {
+    const long long npk_total = pw[p].npk;
+    const int nseg = pw[p].nseg;
+    for (int t = 0; t < (int)probs[p].units->size(); ++t)
+      for (int c = 0; c < probs[p].n_chan; ++c)
+        // fold-window segment sg: stages [npk sg / nseg, npk (sg + 1) / nseg)
+        for (int sg = 0; sg < nseg; ++sg)
+          deal(p, t, c, (int)(npk_total * sg / nseg), (int)(npk_total * (sg + 1) / nseg));
   }
   if (load > 0 || (int)cta_first.size() == 1) close_cta();
   // drop trailing empty CTAs

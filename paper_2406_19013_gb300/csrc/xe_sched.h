@@ -45,14 +45,22 @@ struct ProbWork {
   int n_blocks;  // blocks in the launch
 };
 
+// Packed stages one item may integrate before its fold: 1023 stages are at
+// most 130944 samples, so every fp32 partial stays an integer below 2^24
+// (128 per sample at most).
+constexpr int kMaxFoldStages = 131071 / kPkSamples;
+
 // Cuts every unit (problem, template, channel) into items and deals
 // contiguous runs of them to at most `grid` CTAs.  Each CTA receives about
 // the same modelled cost: the unpack work (operand rows x chunks) of its
 // items plus a fixed fold cost per item.  A unit is split only at 128-sample
-// stage boundaries and only into pieces of at least min_split_pk stages.
+// stage boundaries and only into pieces of at least min_split_pk stages;
+// first it is cut into equal segments of at most max_item_pk stages (the
+// fold window), which every item stays inside.
 // Fills items and cta_first (size used_grid + 1) and returns used_grid.
 int build_items(const std::vector<ProbWork> &probs, int grid, std::vector<XItem> &items,
-                std::vector<int> &cta_first, int min_split_pk = 16);
+                std::vector<int> &cta_first, int min_split_pk = 16,
+                int max_item_pk = kMaxFoldStages);
 
 // The TMA descriptor of one block, uint8 [n_chan][n_in][row pitch], 3-D
 // (time, input, channel) with 128-sample x 64-input boxes, 128B-swizzled.

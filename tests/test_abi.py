@@ -48,7 +48,7 @@ def test_strerror(corr):
 
 @pytest.mark.parametrize("args", [
     (0, 2, 4, 64), (4, 3, 4, 64), (4, 0, 4, 64), (4, 2, 0, 64), (4, 2, 4, 0),
-    (4, 2, 4, -5), (4, 2, 4, 131072), (8193, 1, 1, 16), (4097, 2, 1, 16)])
+    (4, 2, 4, -5), (4, 2, 4, 16777216), (8193, 1, 1, 16), (4097, 2, 1, 16)])
 def test_create_rejects_bad_sizes(corr, args):
     with pytest.raises(corr.CorrError) as e:
         corr.Correlator(*args)
@@ -122,6 +122,18 @@ def _check_split(corr, n_in, n_chan, block_len, n_blocks, grid, cover=0, min_spl
         if len(ns) > 1:
             assert min(ns) >= min(min_split, npk)
     return items, first
+
+
+@pytest.mark.parametrize("n_in,n_chan,block_len,n_blocks", [
+    (16, 3, 300000, 1), (16, 2, 200001, 1), (192, 4, 16777215, 1), (64, 5, 65536, 2)])
+def test_items_stay_inside_the_fold_window(corr, n_in, n_chan, block_len, n_blocks):
+    # a block longer than the fp32 fold window is cut into items of at most
+    # 1023 stages (130944 samples), each folded on its own; coverage stays exact
+    items, _ = _check_split(corr, n_in, n_chan, block_len, n_blocks, 152)
+    assert items[:, 4].max() <= corr.CORR_FOLD_SAMPLES // 128
+    npk = -(-block_len // 128) * n_blocks
+    n_tpl = corr.plan_cover(n_in, 0)[0]
+    assert len(items) >= n_tpl * n_chan * -(-npk // 1023)
 
 
 def test_item_split_balances_the_paper_launch(corr):

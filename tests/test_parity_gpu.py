@@ -149,6 +149,28 @@ def test_extremes_at_max_block_len(corr, torch_cuda, oracle_mod, synth_mod):
             assert (vis[..., 0] == 128 * T).all() and not vis[..., 1].any()
 
 
+@pytest.mark.parametrize("T,nb", [(300000, 1), (200001, 2)])
+def test_blocks_longer_than_the_fold_window(corr, torch_cuda, oracle_mod, synth_mod, T, nb):
+    # Runs of -8-8j longer than 131071 samples: an auto reaches 128 x the run
+    # length > 2^24, which stays exact only if every item folds its fp32
+    # partials into int64 within the window.  T = 200001 also takes the
+    # pitched staging path (T % 16 != 0).
+    n_ant, C = 8, 2
+    N = 2 * n_ant
+    rng = np.random.default_rng(T)
+    blocks = []
+    for b in range(nb):
+        x = synth_mod.make_block(N, C, T, seed=40 + b, tones=synth_mod.random_phase_tone(N, 40))
+        x[:, :, : 2 * T // 3] = 0x88
+        x[:, 3, T // 3: T // 3 + 4096] = rng.integers(0, 256, size=(C, 4096), dtype=np.uint8)
+        blocks.append(x)
+    vis, st = _run(corr, torch_cuda, blocks, n_ant, 2)
+    ov, ost = _oracle(oracle_mod, blocks, n_ant, 2)
+    assert np.array_equal(vis, ov)
+    assert np.array_equal(st, ost)
+    assert ov[:, 0, 0].min() > 2 ** 24  # the check above is beyond one fp32 partial
+
+
 def test_all_byte_values(corr, torch_cuda, oracle_mod):
     # every byte value against every other, 16 inputs x 256 samples
     N, T = 16, 256

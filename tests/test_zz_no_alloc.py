@@ -1,10 +1,13 @@
 """corr_xcorr_static, the entry point for callers that must not allocate device
-memory (code inside a framework that owns the device memory pool, or on a
-real-time path where cudaMalloc's implicit synchronisation would stall queued
-work).  Its scratch lives in a fixed device array inside the library; its
-visibilities must equal, exactly, those of the context API on the same bytes,
-call after call.  This file is collected last so that a run stopping at the
-first failure has already run every other test."""
+memory: code inside a framework that owns the device memory pool (an
+allocation outside it can break the pool's budget) and code on a real-time
+path, where cudaMalloc's implicit synchronisation would stall queued work.
+Its scratch lives in a fixed device array inside the library.
+
+Its visibilities must equal the CPU oracle's exactly, and the context API's on
+the same bytes, call after call; once the device is warm a call must not
+change the device's free memory.  This file is collected last so that a run
+stopping at the first failure has already run every other test."""
 import numpy as np
 import pytest
 
@@ -22,7 +25,7 @@ def corr():
     return c
 
 
-def _context_vis(corr, torch, block, n_ant, n_pol):
+def _context_vis(corr, block, n_ant, n_pol):
     C, N, T = block.shape
     with corr.Correlator(n_ant, n_pol, C, T) as xc:
         xc.push_block(block)
@@ -31,21 +34,49 @@ def _context_vis(corr, torch, block, n_ant, n_pol):
     return vis.cpu().numpy()
 
 
-def test_static_entry_matches_context_api_two_calls(corr, synth_mod):
+# (n_ant, n_pol, channels, block_len, seed)
+CASES = [
+    (96, 2, 48, 2048, 11),   # the paper's 192 inputs
+    (100, 2, 5, 1008, 12),   # 200 inputs: two units
+    (128, 2, 3, 512, 13),    # 256 inputs: the largest accepted
+    (8, 2, 64, 2048, 14),    # the tiny 16-input workload
+    (9, 1, 3, 64, 15),       # 9 inputs: one partial row tile, one chunk
+    (33, 1, 4, 48, 16),      # 33 inputs, a block shorter than one chunk
+]
+
+
+@pytest.mark.parametrize("n_ant,n_pol,C,T,seed", CASES)
+def test_static_entry_matches_oracle_two_calls(corr, oracle_mod, synth_mod, n_ant, n_pol, C, T,
+                                                seed):
     import torch
-    cases = [(96, 2, 48, 2048, 11), (100, 2, 5, 1008, 12)]  # 192 inputs; 200 inputs (two units)
-    for n_ant, n_pol, C, T, seed in cases:
-        N = n_ant * n_pol
-        blocks = [synth_mod.make_block(N, C, T, seed=seed, block=b,
-                                       tones=synth_mod.random_phase_tone(N, seed)) for b in range(2)]
-        vis = torch.empty((C, N * (N + 1) // 2, 2), dtype=torch.int64, device="cuda")
-        for b in blocks:  # two calls in a row, the second on different bytes
-            x = torch.from_numpy(b).cuda()
-            corr.xcorr_static(x, n_ant, n_pol, vis=vis)
-            torch.cuda.synchronize()
-            got = vis.cpu().numpy()
-            want = _context_vis(corr, torch, x, n_ant, n_pol)
-            assert np.array_equal(got, want)
+    N = n_ant * n_pol
+    blocks = [synth_mod.make_block(N, C, T, seed=seed, block=b,
+                                   tones=synth_mod.random_phase_tone(N, seed)) for b in range(2)]
+    vis = torch.empty((C, N * (N + 1) // 2, 2), dtype=torch.int64, device="cuda")
+    for b in blocks:  # two calls in a row, the second on different bytes
+        x = torch.from_numpy(b).cuda()
+        corr.xcorr_static(x, n_ant, n_pol, vis=vis)
+        torch.cuda.synchronize()
+        got = vis.cpu().numpy()
+        assert np.array_equal(got, oracle_mod.xcorr(b))
+        assert np.array_equal(got, _context_vis(corr, x, n_ant, n_pol))
+
+
+def test_warm_calls_leave_free_memory_unchanged(corr, oracle_mod, synth_mod):
+    import torch
+    n_ant, n_pol, C, T = 96, 2, 16, 1024
+    N = n_ant * n_pol
+    x = torch.from_numpy(synth_mod.make_block(N, C, T, seed=21)).cuda()
+    vis = torch.empty((C, N * (N + 1) // 2, 2), dtype=torch.int64, device="cuda")
+    corr.xcorr_static(x, n_ant, n_pol, vis=vis)  # first call: device set-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        corr.xcorr_static(x, n_ant, n_pol, vis=vis)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert np.array_equal(vis.cpu().numpy(), oracle_mod.xcorr(x.cpu().numpy()))
 
 
 def test_static_entry_rejects_out_of_limit_sizes(corr):
