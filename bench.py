@@ -391,6 +391,101 @@ def run_ours(args):
     return 0
 
 
+def run_large_n(args):
+    """The large-N configuration: 1024 dual-pol antennas (2048 inputs, 2.1 M
+    pairs with autos), 256 channels, 4096-sample blocks with three injected
+    tones at distinct index-space phase gradients; one step integrates 16
+    blocks (two launches of eight) into the 8.6 GB int64 buffer and dumps
+    visibilities and full Stokes."""
+    import torch
+
+    from paper_2406_19013_gb300 import Correlator, build
+    from paper_2406_19013_gb300.corr import plan
+    from synth import synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    w = synth.workload("large_n", seed=1)
+    n_in, C, T, nb = w.n_in, w.n_chan, w.block_len, w.n_blocks
+    pairs = n_in * (n_in + 1) // 2
+    apairs = w.n_ant * (w.n_ant + 1) // 2
+    cmac_block = pairs * C * T
+    t0 = time.perf_counter()
+    ring = []
+    for r in range(max(1, args.ring)):
+        hb = torch.empty((C, n_in, T), dtype=torch.uint8, pin_memory=True)
+        w.block(r, out=hb.numpy())
+        ring.append(hb.to(dev))
+        del hb
+    log(f"[bench] large_n: generated {len(ring)} blocks in {time.perf_counter() - t0:.1f} s")
+    xc = Correlator(w.n_ant, w.n_pol, C, T)
+    vis = torch.empty((C, pairs, 2), dtype=torch.int64, device=dev)
+    stk = torch.empty((C, apairs, 4, 2), dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    group = 8
+    n_groups = nb // group
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(n_groups)] for _ in range(args.steps)]
+
+    def step(s, record):
+        for gi in range(n_groups):
+            blks = [ring[(s * nb + gi * group + b) % len(ring)] for b in range(group)]
+            if record:
+                ev[s][gi][0].record(stream)
+            xc.push_blocks(blks, stream)
+            if record:
+                ev[s][gi][1].record(stream)
+        xc.dump(vis, stk, stream=stream)
+
+    for s in range(args.warmup):
+        step(s, False)
+    xc.check()
+    torch.cuda.synchronize()
+    peak, peak_src = fp8_peak()
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = xc.launch_count()
+    a.record(stream)
+    for s in range(args.steps):
+        step(s, True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    xc.check()
+    n_launch = xc.launch_count() - n0
+    xc.close()
+    ms = a.elapsed_time(b)
+    value = cmac_block * nb * args.steps / (ms / 1e3) / 1e12
+    launch_ms = [x.elapsed_time(y) for row in ev for x, y in row]
+    launch_avg = sum(launch_ms) / len(launch_ms)
+    useful = cmac_block * group * OPS_PER_CMAC
+    _, issued_per, _ = plan(n_in)
+    issued = issued_per * C * T * group * OPS_PER_CMAC
+    achieved = useful / (launch_avg / 1e3) / 1e12
+    line = {
+        "metric": "X-engine Tera-CMAC/s at 2048 inputs", "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e5m2",
+        "data": "synthetic",
+        "config": {"workload": "large-N X-engine: 1024 dual-pol antennas (2048 inputs, 2098176 "
+                               "pairs with autos), 256 channels, 4096-sample blocks of 4+4-bit "
+                               "samples with 3 gradient tones, 16 blocks integrated into int64 "
+                               "(8.6 GB) then dumped as visibilities + full Stokes",
+                   "ring_blocks": len(ring), "l2": "inputs larger than L2: 2.15 GB per block"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "xengine_cmac_kernel",
+                     "launch_ms": launch_avg, "peak_source": peak_src,
+                     "useful_over_issued": useful / issued, "blocks_per_launch": group},
+        "gpu_launches": n_launch, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batched(args):
     """A batch of 64 independent correlators (input counts 32..512, 16..1024
     channels, 256..16384-sample blocks) integrated by corr_batch_push, against
@@ -741,10 +836,11 @@ def main():
     ap.add_argument("--group", type=int, default=8, help="blocks per corr_push_blocks call")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-channels", type=int, default=16)
-    ap.add_argument("--workload", choices=["paper", "batched", "corner_turn", "served",
-                                           "fengine"],
+    ap.add_argument("--workload", choices=["paper", "large_n", "batched", "corner_turn",
+                                           "served", "fengine"],
                     default="paper",
-                    help="paper: the 192-input integration (default); batched: 64 mixed "
+                    help="paper: the 192-input integration (default); large_n: 2048 inputs, "
+                         "256 channels, 16 x 4096-sample blocks; batched: 64 mixed "
                          "correlators in shared launches; corner_turn: the device reorder "
                          "of F-engine-order blocks; served: arrivals from host memory, "
                          "latency percentiles; fengine: the GPU F-engine")
@@ -760,6 +856,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "large_n":
+        return run_large_n(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "corner_turn":

@@ -16,8 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcorr.so")
-SOURCES = ["xengine.cu", "dump.cu", "corr.cu", "corr_static.cu", "xe_sched.cu", "batch.cu", "corner_turn.cu", "server.cu", "fengine.cu", "mma_peak.cu"]
-HEADERS = ["ptx.cuh", "xe_internal.h", "xe_sched.h"]
+SOURCES = ["xengine.cu", "xengine_tm.cu", "dump.cu", "corr.cu", "corr_static.cu", "xe_sched.cu", "batch.cu", "corner_turn.cu", "server.cu", "fengine.cu", "mma_peak.cu"]
+HEADERS = ["ptx.cuh", "xe_internal.h", "xe_sched.h", "xe_unpack.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-I", INCLUDE]

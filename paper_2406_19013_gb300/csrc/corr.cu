@@ -39,6 +39,7 @@ struct corr_ctx {
   ItemPlan plans[xe::kMaxBlocksPerLaunch + 1];
   int smem_bytes, z_stages, pk_stages;
   uint32_t z_stage_bytes, pk_stage_bytes;
+  int tm;  // 1: the TMEM-operand kernel (xengine_tm.cu) runs this context's launches
   int pitch;           // row pitch of the staged block (block_len rounded up to 16)
   uint8_t *d_pitched;  // [n_chan][n_in][pitch] when block_len % 16 != 0
   uint8_t *d_turned;   // [n_chan][n_in][pitch]: corner-turned blocks (allocated on first use)
@@ -91,6 +92,54 @@ int free_ctx(corr_ctx *ctx) {
   cudaFree(ctx->d_stokes_out);
   delete ctx;
   return CORR_OK;
+}
+
+// Which CMAC kernel a context of n_in inputs runs: the TMEM-operand kernel
+// (xengine_tm.cu) for two row tiles (65..128 inputs), where it was measured
+// 5 % faster than the all-shared-memory kernel (xengine.cu), which runs
+// everything else (at 192 inputs it was 9 % faster than the TMEM-operand
+// one).  CORR_CMAC_KERNEL=tm or =smem overrides the choice.
+bool use_tm_kernel(int n_in) {
+  const char *e = std::getenv("CORR_CMAC_KERNEL");
+  if (e && std::strcmp(e, "tm") == 0) return true;
+  if (e && std::strcmp(e, "smem") == 0) return false;
+  return n_in > xe::kTileInputs && n_in <= 2 * xe::kTileInputs;
+}
+
+// Shared-memory stages of the TMEM-operand kernel for n_in inputs: operand
+// stages of G.z_rows rows (TmGeom), at most as many as the TMEM ring has
+// slots, and packed stages of S = 64 n_rt rows of 128 bytes: three operand
+// stages first, then packed stages up to eight, then operand stages while
+// they fit.  Also returns the one window unit the item split models (its
+// cost: operand rows written per chunk).  False above three row tiles or if
+// two of each stage do not fit.
+bool tm_stage_layout(int n_in, int smem_optin, xe::StageLayout *out, std::vector<XUnit> *units) {
+  if (n_in > xe::kTmMaxInputs) return false;
+  const xe::TmGeom G = xe::tm_geom(n_in);
+  const int n_st = xe::kTileInputs * G.n_rt;
+  const int zb = G.z_rows * 128, pb = n_st * xe::kPackedRowBytes;
+  const int zmax = std::min(xe::kMaxZStages, (xe::kTmemCols - G.a_base) / xe::kTmSlotCols);
+  const int avail = smem_optin - 1024 - xe::kBarrierBytes;
+  if (zmax < 2 || 2 * zb + 2 * pb > avail) return false;
+  int zs = std::min(zmax, 3);
+  while (zs > 2 && zs * zb + 2 * pb > avail) --zs;
+  const int ps = std::min(xe::kMaxPkStages, (avail - zs * zb) / pb);
+  while (zs < zmax && (zs + 1) * zb + ps * pb <= avail) ++zs;
+  xe::StageLayout L;
+  L.z_stages = zs;
+  L.pk_stages = ps;
+  L.z_stage_bytes = (uint32_t)zb;
+  L.pk_stage_bytes = (uint32_t)pb;
+  L.smem_bytes = 1024 + xe::kBarrierBytes + zs * zb + ps * pb;
+  // one CTA per SM: the kernel holds all 512 TMEM columns
+  L.smem_bytes = std::min(std::max(L.smem_bytes, smem_optin / 2 + 1024), smem_optin);
+  *out = L;
+  XUnit u;
+  std::memset(&u, 0, sizeof(u));
+  u.z_rows = 2 * n_st;
+  u.work = G.acc_cols;
+  units->assign(1, u);
+  return true;
 }
 
 size_t block_bytes(const corr_ctx *c) {
@@ -167,6 +216,19 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
   ctx->z_stage_bytes = L.z_stage_bytes;
   ctx->pk_stage_bytes = L.pk_stage_bytes;
   ctx->smem_bytes = L.smem_bytes;
+  // the TMEM-operand kernel where it is the faster one (up to three row
+  // tiles); the item split then models its one window unit
+  std::vector<XUnit> tm_units;
+  xe::StageLayout TL;
+  if (use_tm_kernel(ctx->n_in) && tm_stage_layout(ctx->n_in, smem_optin, &TL, &tm_units)) {
+    ctx->tm = 1;
+    ctx->z_stages = TL.z_stages;
+    ctx->pk_stages = TL.pk_stages;
+    ctx->z_stage_bytes = TL.z_stage_bytes;
+    ctx->pk_stage_bytes = TL.pk_stage_bytes;
+    ctx->smem_bytes = TL.smem_bytes;
+  }
+  const std::vector<XUnit> &plan_units = ctx->tm ? tm_units : units;
   // a fold must come before 2^24 / 128 samples have been accumulated in
   // fp32: launches of several blocks stay within that window, and the item
   // split cuts a longer block into pieces that each fold on their own
@@ -207,7 +269,7 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
     std::vector<xe::XItem> items;
     std::vector<int> first;
     ItemPlan &pl = ctx->plans[nb];
-    pl.grid = xe::build_items({{&units, n_chan, block_len, nb}}, ctx->n_sm, items, first);
+    pl.grid = xe::build_items({{&plan_units, n_chan, block_len, nb}}, ctx->n_sm, items, first);
     if ((rc = cuda_err(cudaMalloc(&pl.d_items, items.size() * sizeof(xe::XItem)))) != CORR_OK ||
         (rc = cuda_err(cudaMalloc(&pl.d_cta_first, first.size() * sizeof(int)))) != CORR_OK ||
         (rc = cuda_err(cudaMemcpy(pl.d_items, items.data(), items.size() * sizeof(xe::XItem),
@@ -223,6 +285,7 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
       (rc = cuda_err(cudaMemcpy(ctx->d_units, units.data(), units.size() * sizeof(XUnit),
                                 cudaMemcpyHostToDevice))) != CORR_OK ||
       (rc = cuda_err(xe::cmac_set_smem(smem_optin))) != CORR_OK ||
+      (rc = cuda_err(xe::cmac_tm_set_smem(smem_optin))) != CORR_OK ||
       (rc = cuda_err(cudaDeviceSynchronize())) != CORR_OK) {
     free_ctx(ctx);
     return rc;
@@ -260,7 +323,8 @@ int launch_staged(corr_ctx *ctx, const uint8_t *const *staged, int nb, cudaStrea
   const ItemPlan &pl = ctx->plans[nb];
   p.items = pl.d_items;
   p.cta_first = pl.d_cta_first;
-  if ((rc = cuda_err(xe::launch_cmac(maps, p, pl.grid, ctx->smem_bytes, st))) != CORR_OK)
+  if ((rc = cuda_err(ctx->tm ? xe::launch_cmac_tm(maps, p, pl.grid, ctx->smem_bytes, st)
+                            : xe::launch_cmac(maps, p, pl.grid, ctx->smem_bytes, st))) != CORR_OK)
     return rc;
   ctx->launches++;
   if (!selftest_timeout_ns) ctx->samples += (long long)nb * ctx->block_len;

@@ -122,12 +122,67 @@ struct XMapsT {
 using XMaps = XMapsT<kMaxMaps>;
 using XBatchMaps = XMapsT<kMaxBatchMaps>;
 
+// Geometry of the TMEM-operand kernel (xengine_tm.cu) for one problem of
+// n_in <= kTmMaxInputs inputs: one window unit of n_rt row tiles.  Row tile 0
+// (inputs 0..63) reads its row operand from a TMEM ring of 32-column slots
+// from column a_base; tiles 1 and 2 read theirs from shared memory.  Tile t
+// has nt[t] columns and its accumulator at TMEM column acc[t] (the largest
+// tile first).  The shared-memory operand stage holds, in units of 64 rows of
+// 128 bytes (Q = [b, -a] rows, A = [a, b] rows):
+//   n_rt = 1:  A(0..63)
+//   n_rt = 2:  Q(64..127) A(64..127) A(0..63)
+//   n_rt = 3:  Q(64..127) A(64..127) A(0..63) A(128..191) Q(128..191)
+// so tile 1's row operand is [Q; A] of its inputs, tile 2's [A; Q], and the
+// column operands of tiles 0, 1, 2 are the contiguous row ranges A(0..63),
+// A(64..127) A(0..63) and A(64..127) A(0..63) A(128..191): one MMA per tile
+// per K slice.  Column n of tiles 1 and 2 is input 64 + n for n < 64, n - 64
+// for 64 <= n < 128, n above.
+constexpr int kTmMaxInputs = 3 * kTileInputs;
+struct TmGeom {
+  int n_rt, n16;
+  int nt[3], acc[3];
+  int acc_cols, a_base;
+  int z_rows, row_q1, row_a1, row_a0, row_a2, row_q2;  // operand-stage rows
+};
+__host__ __device__ inline TmGeom tm_geom(int n_in) {
+  TmGeom g;
+  g.n16 = (n_in + 15) / 16 * 16;
+  g.n_rt = (n_in + kTileInputs - 1) / kTileInputs;
+  g.nt[0] = g.n16 < kTileInputs ? g.n16 : kTileInputs;
+  g.nt[1] = g.n_rt >= 2 ? 2 * kTileInputs : 0;
+  g.nt[2] = g.n_rt >= 3 ? g.n16 : 0;
+  g.acc[2] = 0;
+  g.acc[1] = g.nt[2];
+  g.acc[0] = g.nt[2] + g.nt[1];
+  g.acc_cols = g.acc[0] + g.nt[0];
+  g.a_base = (g.acc_cols + 31) / 32 * 32;
+  const int T = kTileInputs;
+  if (g.n_rt == 1) {
+    g.row_a0 = 0;
+    g.row_q1 = g.row_a1 = g.row_a2 = g.row_q2 = 0;
+    g.z_rows = T;
+  } else {
+    g.row_q1 = 0;
+    g.row_a1 = T;
+    g.row_a0 = 2 * T;
+    g.row_a2 = 3 * T;
+    g.row_q2 = 4 * T;
+    g.z_rows = g.n_rt == 2 ? 3 * T : 5 * T;
+  }
+  return g;
+}
+// TMEM columns of one ring slot: row tile 0's operand for one 64-sample chunk.
+constexpr int kTmSlotCols = 32;
+
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_cmac(const XMaps &maps, const XParams &p, int grid, int smem_bytes,
                         cudaStream_t stream);
 cudaError_t launch_cmac_batch(const XBatchMaps &maps, const XParams &p, int grid, int smem_bytes,
                               cudaStream_t stream);
 cudaError_t cmac_set_smem(int smem_bytes);
+cudaError_t launch_cmac_tm(const XMaps &maps, const XParams &p, int grid, int smem_bytes,
+                           cudaStream_t stream);
+cudaError_t cmac_tm_set_smem(int smem_bytes);
 cudaError_t launch_dump(int64_t *acc, int64_t *vis, int64_t *stokes, int n_ant, int n_pol,
                         int n_chan, cudaStream_t stream, int grid);
 cudaError_t launch_pitch(const uint8_t *src, uint8_t *dst, long long rows, int T, int pitch,

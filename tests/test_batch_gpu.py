@@ -121,7 +121,7 @@ def test_batch_rejects(corr):
     with pytest.raises(corr.CorrError):
         corr.Batch([(8, 3, 4, 64)])
     with pytest.raises(corr.CorrError):
-        corr.Batch([(8, 2, 4, 200000)])
+        corr.Batch([(8, 2, 4, corr.CORR_MAX_BLOCK_LEN + 1)])
     with corr.Batch([(8, 2, 4, 64)]) as bt:
         x = torch.zeros(4 * 16 * 64 + 16, dtype=torch.uint8, device="cuda")
         lib = corr.load()

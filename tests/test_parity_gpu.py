@@ -406,3 +406,31 @@ def test_corner_turn_paper_block(corr, torch_cuda, oracle_mod, synth_mod):
     x_tcn = np.ascontiguousarray(np.transpose(x, (2, 0, 1)))
     got = corr.corner_turn(torch.from_numpy(x_tcn).cuda()).cpu().numpy()
     assert np.array_equal(got, oracle_mod.corner_turn(x_tcn))
+
+
+@pytest.mark.parametrize("kernel", ["tm", "smem"])
+@pytest.mark.parametrize("n_ant,n_pol,C,T,nb", [
+    (1, 1, 2, 64, 1),        # one input, one row tile
+    (9, 1, 3, 100, 2),       # ragged N and T (pitched staging)
+    (32, 2, 4, 2048, 3),     # N = 64: one full row tile
+    (65, 1, 3, 512, 2),      # N = 65: a second, almost empty row tile
+    (64, 2, 3, 4096, 2),     # N = 128: two row tiles, the second from TMEM
+    (75, 2, 5, 1024, 3),     # N = 150: three row tiles, the last ragged
+    (96, 2, 6, 8192, 2),     # N = 192: the paper's inputs
+])
+def test_both_cmac_kernels_match_oracle(corr, torch_cuda, oracle_mod, synth_mod, monkeypatch,
+                                        kernel, n_ant, n_pol, C, T, nb):
+    # CORR_CMAC_KERNEL=tm selects, at corr_create, the kernel that keeps row
+    # tile 0's row operand in TMEM (up to three row tiles); =smem the
+    # all-shared-memory kernel.  Both must give the oracle's visibilities
+    # exactly.
+    monkeypatch.setenv("CORR_CMAC_KERNEL", kernel)
+    N = n_ant * n_pol
+    tones = synth_mod.random_phase_tone(N, 17)
+    blocks = [synth_mod.make_block(N, C, T, seed=300 + N, block=b, tones=tones) for b in range(nb)]
+    blocks[0][:, :, : T // 2] = 0x88  # -8-8j runs: the largest products
+    vis, st = _run(corr, torch_cuda, blocks, n_ant, n_pol)
+    ov, ost = _oracle(oracle_mod, blocks, n_ant, n_pol)
+    assert np.array_equal(vis, ov)
+    if n_pol == 2:
+        assert np.array_equal(st, ost)
