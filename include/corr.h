@@ -262,10 +262,19 @@ int corr_corner_turn(const uint8_t *d_src, uint8_t *d_dst, int n_in, int n_chan,
 
 /*
  * As corr_push_block for a block in F-engine order, uint8
- * [block_len][n_chan][N] (d_src, 4-byte aligned).  The block is corner-turned
- * into a context-owned buffer, which is allocated on the first call and freed
- * by corr_destroy, and then integrated.  d_src may be reused once the stream
- * has executed the call.  Errors: as corr_push_block, plus CORR_ENOMEM.
+ * [block_len][n_chan][N] (d_src, 4-byte aligned): the Transpose step of
+ * Sec. 2.1 and the correlation in one call.
+ *   - When N is a multiple of 16, d_src is 16-byte aligned and the context
+ *     runs the all-shared-memory CMAC kernel (every N outside 65..128, or
+ *     CORR_CMAC_KERNEL=smem), the CMAC kernel stages the block in this order
+ *     itself: its TMA boxes are [128 samples][64 inputs] of one channel and
+ *     the unpack transposes them on chip.  One launch; every byte is read
+ *     once.
+ *   - Otherwise the block is first corner-turned into a context-owned buffer
+ *     (allocated on the first such call, freed by corr_destroy), then
+ *     integrated: two launches.
+ * d_src may be reused once the stream has executed the call.  Errors: as
+ * corr_push_block, plus CORR_ENOMEM.
  */
 int corr_push_block_tcn(corr_ctx *ctx, const uint8_t *d_src, void *stream);
 

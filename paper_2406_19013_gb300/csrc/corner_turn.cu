@@ -24,6 +24,7 @@
 #include <cstdint>
 
 #include "xe_internal.h"
+#include "xe_unpack.cuh"
 
 namespace xe {
 
@@ -45,19 +46,6 @@ __device__ __forceinline__ uint4 load_src16(const uint8_t *src, long long row_of
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// 4 x 4 byte transpose: out[j] byte k = in[k] byte j.
-__device__ __forceinline__ void transpose4(uint32_t i0, uint32_t i1, uint32_t i2, uint32_t i3,
-                                           uint32_t &o0, uint32_t &o1, uint32_t &o2,
-                                           uint32_t &o3) {
-  const uint32_t lo01 = __byte_perm(i0, i1, 0x5140);  // i0.b0 i1.b0 i0.b1 i1.b1
-  const uint32_t hi01 = __byte_perm(i0, i1, 0x7362);  // i0.b2 i1.b2 i0.b3 i1.b3
-  const uint32_t lo23 = __byte_perm(i2, i3, 0x5140);
-  const uint32_t hi23 = __byte_perm(i2, i3, 0x7362);
-  o0 = __byte_perm(lo01, lo23, 0x5410);
-  o1 = __byte_perm(lo01, lo23, 0x7632);
-  o2 = __byte_perm(hi01, hi23, 0x5410);
-  o3 = __byte_perm(hi01, hi23, 0x7632);
-}
 
 // Word w (4 samples) of tile row r: chunk (w / 4) is stored at chunk
 // (w / 4) ^ ((r / 16) & 7).

@@ -302,7 +302,7 @@ namespace {
 // ctx->pitch bytes apart.  selftest_timeout_ns > 0 runs the failure-detection
 // self-test instead (see corr_selftest_timeout).
 int launch_staged(corr_ctx *ctx, const uint8_t *const *staged, int nb, cudaStream_t st,
-                  unsigned long long selftest_timeout_ns = 0) {
+                  unsigned long long selftest_timeout_ns = 0, bool tcn = false) {
   XParams p;
   std::memset(&p, 0, sizeof(p));
   p.probs = ctx->d_prob;
@@ -316,10 +316,16 @@ int launch_staged(corr_ctx *ctx, const uint8_t *const *staged, int nb, cudaStrea
   xe::XMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   int rc;
-  for (int k = 0; k < nb; ++k)
-    if ((rc = encode_block_map(ctx, staged[k], reinterpret_cast<CUtensorMap *>(maps.m[k]))) !=
-        CORR_OK)
+  p.tcn = tcn ? 1 : 0;
+  for (int k = 0; k < nb; ++k) {
+    if (tcn) {
+      if (!xe::encode_block_map_tcn(staged[k], ctx->block_len, ctx->n_in, ctx->n_chan, maps.m[k]))
+        return CORR_ECUDA;
+    } else if ((rc = encode_block_map(ctx, staged[k], reinterpret_cast<CUtensorMap *>(maps.m[k]))) !=
+               CORR_OK) {
       return rc;
+    }
+  }
   const ItemPlan &pl = ctx->plans[nb];
   p.items = pl.d_items;
   p.cta_first = pl.d_cta_first;
@@ -397,6 +403,11 @@ int corr_selftest_timeout(corr_ctx *ctx, const uint8_t *d_block, int timeout_ms,
 int corr_push_block_tcn(corr_ctx *ctx, const uint8_t *d_src, void *stream) {
   if (!ctx || !d_src || (reinterpret_cast<uintptr_t>(d_src) & 3u)) return CORR_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // The shared-memory kernel stages F-engine-order blocks directly (TMA boxes
+  // of [128 samples][64 inputs], transposed on chip) when the block's strides
+  // allow a tensor map; otherwise the block is turned in HBM first.
+  if (!ctx->tm && ctx->n_in % 16 == 0 && (reinterpret_cast<uintptr_t>(d_src) & 15u) == 0)
+    return launch_staged(ctx, &d_src, 1, st, 0, true);
   int rc;
   if (!ctx->d_turned &&
       (rc = cuda_err(cudaMalloc(&ctx->d_turned, (size_t)ctx->n_chan * ctx->n_in * ctx->pitch))) !=

@@ -109,6 +109,11 @@ struct XParams {
   int z_stages, pk_stages;
   uint32_t z_stage_bytes, pk_stage_bytes;
   int selftest_never;  // failure-detection self-test (see corr_selftest_timeout)
+  // 1: the blocks are in F-engine order, uint8 [time][channel][input], and
+  // their maps are 3-D (input, channel, time) with 64-input x 128-sample
+  // boxes (no swizzle); the unpack transposes them on chip, and operand rows
+  // are rotated within every 8-input group (see xengine.cu)
+  int tcn;
 };
 
 // TMA descriptors (CUtensorMap, 128 bytes each), one per (problem, block) of

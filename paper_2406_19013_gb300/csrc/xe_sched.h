@@ -68,4 +68,10 @@ int build_items(const std::vector<ProbWork> &probs, int grid, std::vector<XItem>
 // unavailable or rejects the arguments.
 bool encode_block_map(const void *base, int block_len, int n_in, int n_chan, int pitch, void *map);
 
+// The TMA descriptor of one block in F-engine order, uint8 [block_len][n_chan]
+// [n_in], 3-D (input, channel, time) with 64-input x 1-channel x 128-sample
+// boxes, no swizzle (each box lands as [128 samples][64 inputs]).  The
+// channel and time strides must be multiples of 16 bytes: n_in % 16 == 0.
+bool encode_block_map_tcn(const void *base, int block_len, int n_in, int n_chan, void *map);
+
 }  // namespace xe

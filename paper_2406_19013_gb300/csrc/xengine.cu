@@ -70,7 +70,10 @@ __device__ __forceinline__ int chunks_in_pk(const XProb &pb, int kc) {
 
 // kThreads = 32 * 25: warps 0-15 unpack, 16-19 epilogue, 20 TMA, 21-24 MMA.
 // Every role walks the same item list, [cta_first[b], cta_first[b + 1]).
-template <int M>
+// TCN: the blocks are in F-engine order (XParams::tcn), staged and unpacked
+// by the transposing path; a compile-time choice, so that the X-engine-order
+// kernel carries none of that code.
+template <int M, bool TCN>
 __global__ void __launch_bounds__(kThreads, 1)
     xengine_cmac_kernel(const __grid_constant__ XMapsT<M> maps, const XParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -164,9 +167,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t dst0 = smem_u32(pk_buf + (size_t)s * p.pk_stage_bytes);
           for (int r = 0; r < n_reg; ++r) {
             const int in_lo = u->reg[r].in_lo, n_in = u->reg[r].n_in, off = u->reg[r].pk_off;
-            for (int bx = 0; bx < n_in; bx += kTileInputs)
-              tma_load_3d(dst0 + off + bx * kPackedRowBytes, tmap, full, kc * kPkSamples,
-                          in_lo + bx, item.chan);
+            for (int bx = 0; bx < n_in; bx += kTileInputs) {
+              if (TCN)  // (input, channel, time): a [128 samples][64 inputs] box
+                tma_load_3d(dst0 + off + bx * kPackedRowBytes, tmap, full, in_lo + bx, item.chan,
+                            kc * kPkSamples);
+              else        // (time, input, channel): a [64 inputs][128 samples] box
+                tma_load_3d(dst0 + off + bx * kPackedRowBytes, tmap, full, kc * kPkSamples,
+                            in_lo + bx, item.chan);
+            }
           }
           if (++s == p.pk_stages) { s = 0; ph ^= 1u; }
         }
@@ -289,6 +297,48 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (sub >= nch) break;
           if (!mbar_wait(b.z_empty + 8 * zs, zph ^ 1u, abort_flag, to)) { ok = false; break; }
           const uint32_t z_s = z_s0 + (uint32_t)zs * p.z_stage_bytes;
+          if (TCN) {
+            // F-engine order: each 64-input box is [128 samples][64 inputs].
+            // Item (q, j) of a box: inputs 4 q .. 4 q + 3, samples 8 j ..
+            // 8 j + 7 of the chunk; eight 4-byte loads (one sample of four
+            // inputs each), two 4 x 4 byte transposes, and per input two
+            // decoded words: 16 bytes of its A row (and Q row) at K bytes
+            // 16 j .. 16 j + 15.  The half-warp of odd j loads its samples
+            // rotated by one (the same rotation for every input, so a fixed
+            // permutation of K), which puts the two half-warps' rows on
+            // different bank halves.  Within every 8-input group of a region
+            // the operand row of group position pos is (pos + group) % 8: the
+            // eight threads of a store phase then hit eight bank groups.
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+              if (r >= n_reg) break;
+              const XRegion rg = u->reg[r];
+              const int u_it = tid;
+              if (u_it < (rg.n_in / kTileInputs) * 128) {
+                const int box = u_it >> 7, v = u_it & 127, qd = v & 15, j = v >> 4, jj = j & 1;
+                const uint32_t src = pk_s + (uint32_t)rg.pk_off + (uint32_t)box * 8192u +
+                                     (uint32_t)(64 * (kChunkSamples * sub + 8 * j)) + 4u * qd;
+                uint32_t w[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) w[k] = lds32(src + 64u * (uint32_t)((k + jj) & 7));
+                uint32_t lo[4], hi[4];
+                transpose4(w[0], w[1], w[2], w[3], lo[0], lo[1], lo[2], lo[3]);
+                transpose4(w[4], w[5], w[6], w[7], hi[0], hi[1], hi[2], hi[3]);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  uint2 al, ql, ah, qh;
+                  decode_word(lo[e], al, ql);
+                  decode_word(hi[e], ah, qh);
+                  const int i_rel = kTileInputs * box + 4 * qd + e, grp = i_rel >> 3;
+                  const int pos = ((i_rel & 7) + (grp & 3)) & 7;
+                  const int zrow = rg.z_row + (rg.interleaved ? 16 * grp : 8 * grp) + pos;
+                  const uint32_t d = z_s + (uint32_t)zrow * 128u + (uint32_t)((j ^ pos) << 4);
+                  sts128(d, al.x, al.y, ah.x, ah.y);
+                  if (rg.interleaved) sts128_q(d, ql.x, ql.y, qh.x, qh.y);
+                }
+              }
+            }
+          } else {
           // operand chunk `sub` of the packed stage (64 of its 128 samples)
 #pragma unroll
           for (int r = 0; r < 2; ++r) {
@@ -316,6 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 sts128_q(d1, q2.x, q2.y, q3.x, q3.y);
               }
             }
+          }
           }
           fence_proxy_async_smem();
           __syncwarp();
@@ -349,9 +400,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (*abort_flag) break;
       tc_fence_after();
       const int n_seg = u->n_seg;
+      // in F-engine-order launches, lane 16 g + l holds the input at group
+      // position (l - g) % 8 of its 8-input group, and column 8 G + e the one
+      // at (e - G) % 8 (the groups of a row tile or column range start at
+      // multiples of 64 inputs, so only g % 4 and G % 4 matter)
+      const int l_in = TCN ? ((l - (g & 3)) & 7) : l;
       for (int sg = 0; sg < n_seg; ++sg) {
         const XSeg sgm = u->seg[sg];
-        const int i = sgm.row_in0 + 8 * g + l;
+        const int i = sgm.row_in0 + 8 * g + l_in;
         const bool row_ok = i < pb.n_in;
         int64_t *arow = pb.acc + ((long long)c * pb.n_pairs + (long long)i * (i + 1) / 2) * 2;
         for (int cb = 0; cb < sgm.n; cb += 16) {
@@ -370,14 +426,26 @@ __global__ void __launch_bounds__(kThreads, 1)
             im[e] = is_im ? mine : other;
           }
           const int j0 = sgm.col_in0 + cb + (is_im ? 8 : 0);
-          const int nvalid = row_ok ? min(8, i - j0 + 1) : 0;
-          int64_t *ptr = arow + 2 * (long long)j0;
+          if (TCN) {
+            const int rot = ((cb + (is_im ? 8 : 0)) >> 3) & 3;
 #pragma unroll
-          for (int e = 0; e < 8; ++e)
-            if (e < nvalid) {
-              red_add_s64(ptr + 2 * e, re[e]);
-              red_add_s64(ptr + 2 * e + 1, im[e]);
+            for (int e = 0; e < 8; ++e) {
+              const int jj = j0 + ((e - rot) & 7);
+              if (row_ok && jj <= i) {
+                red_add_s64(arow + 2 * (long long)jj, re[e]);
+                red_add_s64(arow + 2 * (long long)jj + 1, im[e]);
+              }
             }
+          } else {
+            const int nvalid = row_ok ? min(8, i - j0 + 1) : 0;
+            int64_t *ptr = arow + 2 * (long long)j0;
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              if (e < nvalid) {
+                red_add_s64(ptr + 2 * e, re[e]);
+                red_add_s64(ptr + 2 * e + 1, im[e]);
+              }
+          }
         }
       }
       tc_fence_before();
@@ -397,22 +465,28 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 cudaError_t cmac_set_smem(int smem_bytes) {
-  cudaError_t e = cudaFuncSetAttribute(xengine_cmac_kernel<kMaxMaps>,
+  cudaError_t e = cudaFuncSetAttribute(xengine_cmac_kernel<kMaxMaps, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(xengine_cmac_kernel<kMaxBatchMaps>,
+  e = cudaFuncSetAttribute(xengine_cmac_kernel<kMaxMaps, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(xengine_cmac_kernel<kMaxBatchMaps, false>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
 }
 
 cudaError_t launch_cmac(const XMaps &maps, const XParams &p, int grid, int smem_bytes,
                         cudaStream_t stream) {
-  xengine_cmac_kernel<kMaxMaps><<<grid, kThreads, smem_bytes, stream>>>(maps, p);
+  if (p.tcn)
+    xengine_cmac_kernel<kMaxMaps, true><<<grid, kThreads, smem_bytes, stream>>>(maps, p);
+  else
+    xengine_cmac_kernel<kMaxMaps, false><<<grid, kThreads, smem_bytes, stream>>>(maps, p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cmac_batch(const XBatchMaps &maps, const XParams &p, int grid, int smem_bytes,
                               cudaStream_t stream) {
-  xengine_cmac_kernel<kMaxBatchMaps><<<grid, kThreads, smem_bytes, stream>>>(maps, p);
+  xengine_cmac_kernel<kMaxBatchMaps, false><<<grid, kThreads, smem_bytes, stream>>>(maps, p);
   return cudaGetLastError();
 }
 

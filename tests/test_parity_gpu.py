@@ -381,21 +381,58 @@ def test_corner_turn_matches_oracle(corr, torch_cuda, oracle_mod, T, C, N):
     assert np.array_equal(got.cpu().numpy(), oracle_mod.corner_turn(x_tcn))
 
 
-@pytest.mark.parametrize("n_ant,n_pol,C,T", [(8, 2, 16, 1024), (65, 2, 3, 1000), (5, 1, 4, 33)])
-def test_push_block_tcn_matches_oracle(corr, torch_cuda, oracle_mod, synth_mod, n_ant, n_pol, C,
-                                       T):
+@pytest.mark.parametrize("n_ant,n_pol,C,T,fused", [
+    (8, 2, 16, 1024, True),    # 16 inputs, one row tile
+    (32, 2, 4, 4096, True),    # 64 inputs
+    (96, 2, 5, 2048, True),    # the paper's 192 inputs: three row tiles
+    (96, 2, 3, 1000, True),    # ragged block length
+    (128, 2, 3, 1000, True),   # 256 inputs: two window units
+    (160, 2, 2, 256, True),    # 320 inputs: row-tile pairs, plain column regions
+    (65, 2, 3, 1000, False),   # 130 inputs: strides not multiples of 16 -> turned in HBM
+    (5, 1, 4, 33, False),      # 5 inputs
+])
+def test_push_block_tcn_matches_oracle(corr, torch_cuda, oracle_mod, synth_mod, monkeypatch, n_ant,
+                                       n_pol, C, T, fused):
+    # Blocks in F-engine order ([time][channel][input], Sec. 2.1's Transpose
+    # input).  Inputs counts that are multiples of 16 are staged straight from
+    # that order by the CMAC kernel (one launch per block, transposed on chip);
+    # the others are corner-turned in HBM first (two launches).
     torch = torch_cuda
+    monkeypatch.setenv("CORR_CMAC_KERNEL", "smem")
     n = n_ant * n_pol
     blocks = [synth_mod.make_block(n, C, T, seed=30 + b, tones=synth_mod.random_phase_tone(n, 30))
               for b in range(2)]
+    blocks[1][:, :, : T // 3] = 0x88
     with corr.Correlator(n_ant, n_pol, C, T) as xc:
+        n0 = xc.launch_count()
         for x in blocks:
             x_tcn = np.ascontiguousarray(np.transpose(x, (2, 0, 1)))  # F-engine order
             xc.push_block_tcn(torch.from_numpy(x_tcn).cuda())
-        vis, _ = xc.dump()
+        launches = xc.launch_count() - n0
+        vis, st = xc.dump()
         xc.check()
-    assert np.array_equal(vis.cpu().numpy(),
-                          oracle_mod.xcorr(blocks[0]) + oracle_mod.xcorr(blocks[1]))
+    ov, ost = _oracle(oracle_mod, blocks, n_ant, n_pol)
+    assert np.array_equal(vis.cpu().numpy(), ov)
+    if n_pol == 2:
+        assert np.array_equal(st.cpu().numpy(), ost)
+    assert launches == (2 if fused else 4)
+
+
+def test_push_block_tcn_all_byte_values(corr, torch_cuda, oracle_mod):
+    # every byte value against every other through the fused F-engine-order path
+    torch = torch_cuda
+    N, T = 64, 512
+    x = np.empty((3, N, T), dtype=np.uint8)
+    for c in range(3):
+        for i in range(N):
+            x[c, i] = (np.arange(T) * (2 * i + 1) + 7 * c + i) % 256
+    with corr.Correlator(N // 2, 2, 3, T) as xc:
+        xc.push_block_tcn(torch.from_numpy(np.ascontiguousarray(np.transpose(x, (2, 0, 1)))).cuda())
+        vis, st = xc.dump()
+        xc.check()
+    ov, ost = _oracle(oracle_mod, [x], N // 2, 2)
+    assert np.array_equal(vis.cpu().numpy(), ov)
+    assert np.array_equal(st.cpu().numpy(), ost)
 
 
 def test_corner_turn_paper_block(corr, torch_cuda, oracle_mod, synth_mod):
