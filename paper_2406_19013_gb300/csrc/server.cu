@@ -6,11 +6,16 @@
 // The paper's pipeline (Sec. 2.3) runs hashpipe threads around ring buffers:
 // a network thread fills block slots, the GPU thread correlates them, an
 // output thread ships integrations.  Here one worker thread owns every CUDA
-// call and drives three streams:
-//   copy    host block -> arena slot (H2D),
-//   compute corner-order pushes and dumps (the CMAC and dump kernels),
-//   out     visibilities -> pinned host result buffer (D2H),
-// so copies of later blocks overlap the correlation of earlier ones.
+// call and drives
+//   copy       host block -> arena slot (H2D), one stream,
+//   compute    one stream per array: its pushes and dumps (the CMAC and dump
+//              kernels), in the order its accumulators need,
+//   out        visibilities -> pinned host result buffer (D2H), one stream,
+// so copies of later blocks overlap the correlation of earlier ones, and the
+// CMAC launches of different arrays run concurrently on the device: a block
+// admitted while another array's work is on the GPU starts as soon as SMs
+// free up instead of queueing behind it (continuous batching of the arrays'
+// requests).
 //
 // Blocks carry (array, sequence number).  Integration k of an array holds
 // sequence numbers [k L, (k + 1) L).  Sums are exact integers, so blocks may
@@ -32,6 +37,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -123,6 +129,8 @@ struct Array {
   corr_array_desc d;
   size_t block_bytes, vis_elems;
   corr_ctx *ctx = nullptr;
+  cudaStream_t s_compute = nullptr;  // this array's pushes and dumps
+  bool stream_shared = false;        // s_compute belongs to array 0
   int64_t *d_vis = nullptr, *h_vis = nullptr;
   long long cur = 0;                 // current integration
   long long closed_below = 0;        // every integration below this is closed
@@ -160,7 +168,7 @@ struct corr_server {
   bool dry = false;
   uint8_t *d_arena = nullptr;
   Arena *arena = nullptr;
-  cudaStream_t s_copy = nullptr, s_compute = nullptr, s_out = nullptr;
+  cudaStream_t s_copy = nullptr, s_out = nullptr;
   std::thread worker;
   std::mutex mu;
   std::condition_variable cv_work, cv_results;
@@ -303,10 +311,10 @@ bool corr_server::progress(int ai) {
     Blk &b = bk.second;
     if (b.state != kCopied) continue;
     if (!dry) {
-      if (cudaStreamWaitEvent(s_compute, b.copied, 0) != cudaSuccess ||
-          corr_push_block(a.ctx, d_arena + b.off, s_compute) != CORR_OK ||
+      if (cudaStreamWaitEvent(a.s_compute, b.copied, 0) != cudaSuccess ||
+          corr_push_block(a.ctx, d_arena + b.off, a.s_compute) != CORR_OK ||
           cudaEventCreateWithFlags(&b.pushed, cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventRecord(b.pushed, s_compute) != cudaSuccess) {
+          cudaEventRecord(b.pushed, a.s_compute) != cudaSuccess) {
         error = CORR_ECUDA;
         return false;
       }
@@ -344,8 +352,8 @@ bool corr_server::progress(int ai) {
   }
   res.vis = dry ? nullptr : a.h_vis;
   if (!dry) {
-    if (corr_dump(a.ctx, a.d_vis, nullptr, s_compute) != CORR_OK ||
-        cudaEventRecord(a.dumped, s_compute) != cudaSuccess ||
+    if (corr_dump(a.ctx, a.d_vis, nullptr, a.s_compute) != CORR_OK ||
+        cudaEventRecord(a.dumped, a.s_compute) != cudaSuccess ||
         cudaStreamWaitEvent(s_out, a.dumped, 0) != cudaSuccess ||
         cudaMemcpyAsync(a.h_vis, a.d_vis, a.vis_elems * sizeof(int64_t), cudaMemcpyDeviceToHost,
                         s_out) != cudaSuccess ||
@@ -449,9 +457,11 @@ void free_server(corr_server *s) {
   }
   if (!s->dry) {
     if (s->s_copy) cudaStreamSynchronize(s->s_copy);
-    if (s->s_compute) cudaStreamSynchronize(s->s_compute);
+    for (Array &a : s->arrays)
+      if (a.s_compute) cudaStreamSynchronize(a.s_compute);
     if (s->s_out) cudaStreamSynchronize(s->s_out);
     for (Array &a : s->arrays) {
+      if (a.s_compute && !a.stream_shared) cudaStreamDestroy(a.s_compute);
       corr_destroy(a.ctx);
       cudaFree(a.d_vis);
       cudaFreeHost(a.h_vis);
@@ -464,7 +474,6 @@ void free_server(corr_server *s) {
     }
     cudaFree(s->d_arena);
     if (s->s_copy) cudaStreamDestroy(s->s_copy);
-    if (s->s_compute) cudaStreamDestroy(s->s_compute);
     if (s->s_out) cudaStreamDestroy(s->s_out);
   }
   delete s->arena;
@@ -513,13 +522,23 @@ int corr_server_create(int n_arrays, const corr_array_desc *desc, size_t arena_b
         (rc = cuda_err(cudaMalloc(&s->d_arena, arena_bytes))) != CORR_OK ||
         (rc = cuda_err(cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking))) !=
             CORR_OK ||
-        (rc = cuda_err(cudaStreamCreateWithFlags(&s->s_compute, cudaStreamNonBlocking))) !=
-            CORR_OK ||
         (rc = cuda_err(cudaStreamCreateWithFlags(&s->s_out, cudaStreamNonBlocking))) != CORR_OK) {
       free_server(s);
       return rc;
     }
+    // CORR_SERVER_ONE_STREAM=1 puts every array's work on one compute stream
+    // (a device queue in arrival order), for comparison
+    const char *one = std::getenv("CORR_SERVER_ONE_STREAM");
+    const bool shared = one && one[0] == '1';
     for (Array &a : s->arrays) {
+      if (shared && &a != &s->arrays[0]) {
+        a.s_compute = s->arrays[0].s_compute;
+        a.stream_shared = true;
+      } else if ((rc = cuda_err(cudaStreamCreateWithFlags(&a.s_compute, cudaStreamNonBlocking))) !=
+                 CORR_OK) {
+        free_server(s);
+        return rc;
+      }
       if ((rc = corr_create(a.d.n_ant, a.d.n_pol, a.d.n_chan, a.d.block_len, &a.ctx)) !=
               CORR_OK ||
           (rc = cuda_err(cudaMalloc(&a.d_vis, a.vis_elems * sizeof(int64_t)))) != CORR_OK ||

@@ -158,6 +158,7 @@ def test_server_rejects(corr):
 # ---------------------------------------------------------------- GPU
 
 @pytest.mark.gpu
+@pytest.mark.gpu
 def test_served_results_match_oracle_under_faults(corr, oracle_mod, synth_mod):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
@@ -195,3 +196,45 @@ def test_served_results_match_oracle_under_faults(corr, oracle_mod, synth_mod):
     assert masks[(0, 0)] == 0b111 and masks[(1, 2)] == 0b11
     assert st["latency_samples"] == st["integrated"] == 14
     assert 0 < st["latency_p50_ms"] <= st["latency_p99_ms"] <= st["latency_max_ms"]
+
+
+@pytest.mark.gpu
+def test_served_mix_equals_each_array_alone(corr, oracle_mod, synth_mod):
+    # Four arrays of different sizes submit their blocks interleaved and
+    # back to back, so their CMAC launches overlap on the device (each array
+    # has its own compute stream).  Every integration must equal, bit for bit,
+    # the same array's integration served alone and the oracle.
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_19013_gb300 import build
+    build.build()
+    arrays = [(16, 2, 96, 2048, 2), (48, 2, 40, 4096, 2), (96, 2, 64, 1024, 2), (8, 1, 200, 512, 2)]
+    n_int = 3
+    blocks = {}
+    for a, (na, npol, nc, T, L) in enumerate(arrays):
+        n = na * npol
+        for seq in range(n_int * L):
+            x = synth_mod.make_block(n, nc, T, seed=70 + a, block=seq,
+                                     tones=synth_mod.random_phase_tone(n, 70 + a))
+            blocks[(a, seq)] = torch.from_numpy(x).pin_memory()
+    arena = 6 * max(b.numel() for b in blocks.values())
+
+    def serve(which):
+        order = [(a, seq) for seq in range(n_int * 2) for a in which]
+        with corr.Server(arrays, arena_bytes=arena, window=2) as srv:
+            for a, seq in order:
+                srv.submit(a, seq, blocks[(a, seq)])
+            srv.flush()
+            res = _drain(srv, n_int * len(which), timeout_s=60)
+            st = srv.stats()
+        assert st["error"] == 0 and len(res) == n_int * len(which)
+        return {(r["array"], r["integration"]): r["vis"].copy() for r in res}
+
+    mixed = serve(range(len(arrays)))
+    for a in range(len(arrays)):
+        alone = serve([a])
+        for k in range(n_int):
+            assert np.array_equal(mixed[(a, k)], alone[(a, k)]), (a, k)
+            want = sum(oracle_mod.xcorr(blocks[(a, 2 * k + q)].numpy()) for q in range(2))
+            assert np.array_equal(mixed[(a, k)], want), (a, k)
