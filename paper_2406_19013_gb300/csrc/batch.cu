@@ -107,6 +107,7 @@ float time_cover(const std::vector<xe::XUnit> &units, int n_in, int C, int T, in
   prob.acc = d_acc;
   prob.n_pairs = (long long)n_in * (n_in + 1) / 2;
   prob.n_in = n_in;
+  prob.n_chan = C;
   prob.chunks_per_block = (T + xe::kChunkSamples - 1) / xe::kChunkSamples;
   prob.pk_per_block = (T + xe::kPkSamples - 1) / xe::kPkSamples;
   prob.map0 = 0;
@@ -276,6 +277,7 @@ int upload_group(corr_batch *b, BGroup &g) {
     p.acc = b->d_acc + in.acc_off;
     p.n_pairs = in.n_pairs;
     p.n_in = in.n_in;
+    p.n_chan = in.n_chan;
     p.chunks_per_block = (in.block_len + xe::kChunkSamples - 1) / xe::kChunkSamples;
     p.pk_per_block = (in.block_len + xe::kPkSamples - 1) / xe::kPkSamples;
     p.map0 = (int)k;

@@ -136,6 +136,7 @@ bool tm_stage_layout(int n_in, int smem_optin, xe::StageLayout *out, std::vector
   *out = L;
   XUnit u;
   std::memset(&u, 0, sizeof(u));
+  u.n_chan = 1;
   u.z_rows = 2 * n_st;
   u.work = G.acc_cols;
   units->assign(1, u);
@@ -256,6 +257,7 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
   prob.acc = ctx->d_acc;
   prob.n_pairs = ctx->n_pairs;
   prob.n_in = ctx->n_in;
+  prob.n_chan = n_chan;
   prob.chunks_per_block = (block_len + xe::kChunkSamples - 1) / xe::kChunkSamples;
   prob.pk_per_block = (block_len + xe::kPkSamples - 1) / xe::kPkSamples;
   prob.map0 = 0;
@@ -562,8 +564,11 @@ int corr_plan_cover(int n_in, int cover_kind, uint8_t *cover, int *n_units,
   if (units.empty()) return CORR_EINVAL;
   long long issued = 0;
   for (const XUnit &u : units) {
+    // a unit of several channels repeats its cover once per channel: count
+    // the first channel's segments
     for (int sg = 0; sg < u.n_seg; ++sg) {
       const XSeg &s = u.seg[sg];
+      if (s.chan_off != 0) continue;
       issued += 64LL * s.n;  // 128 accumulator rows = 64 inputs x (re, im)
       if (!cover) continue;
       // the epilogue's mapping: lane rho holds input row_in0 + 8 (rho / 16) + rho % 8,

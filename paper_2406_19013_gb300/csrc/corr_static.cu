@@ -128,6 +128,7 @@ int plan_single_window(int N, xe::XUnit *units) {
   for (int b = 0; b < n_bins; ++b) {
     xe::XUnit &u = units[b];
     std::memset(&u, 0, sizeof(u));
+    u.n_chan = 1;
     int t_max = 0;
     for (int t = 0; t < n_rt; ++t)
       if (bin_of[t] == b) t_max = std::max(t_max, t);
@@ -215,6 +216,7 @@ extern "C" int corr_xcorr_static(const uint8_t *d_block, int n_ant, int n_pol, i
   prob.acc = d_vis;
   prob.n_pairs = N * (N + 1) / 2;
   prob.n_in = (int)N;
+  prob.n_chan = n_chan;
   prob.chunks_per_block = (block_len + xe::kChunkSamples - 1) / xe::kChunkSamples;
   prob.pk_per_block = (block_len + xe::kPkSamples - 1) / xe::kPkSamples;
   prob.map0 = 0;

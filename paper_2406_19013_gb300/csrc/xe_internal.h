@@ -52,6 +52,7 @@ struct XRegion {
   int interleaved;  // 1: A and Q rows, 0: A rows only
   int z_row;        // first row in the Z stage buffer (multiple of 8)
   int pk_off;       // byte offset in the packed stage buffer
+  int chan_off;     // channel: the item's first channel + chan_off
 };
 
 // One MMA stream of the unit: D[128 x n] += A(tile) * B(cols)^T into TMEM.
@@ -63,10 +64,12 @@ struct XSeg {
   int tmem_col;  // first TMEM column of the accumulator
   int row_in0;   // input index of the tile's first row
   int col_in0;   // input index of the first column
+  int chan_off;  // channel: the item's first channel + chan_off
 };
 
 struct XUnit {
   int n_reg, n_seg;
+  int n_chan;    // channels one unit covers (its regions and segments name the offsets)
   int z_rows;    // rows staged per chunk (sum over regions)
   int pk_bytes;  // packed bytes per chunk (sum over regions)
   int work;      // relative MMA work (sum of n), for ordering
@@ -81,6 +84,7 @@ struct XProb {
   int64_t *acc;          // [n_chan][n_pairs][2]
   long long n_pairs;     // N(N+1)/2
   int n_in;
+  int n_chan;            // channels (a unit's channel past the last is skipped)
   int chunks_per_block;  // ceil(block_len / kChunkSamples)
   int pk_per_block;      // ceil(block_len / kPkSamples)
   int map0;              // the problem's first block map in the launch's map table

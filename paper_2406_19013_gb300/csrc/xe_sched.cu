@@ -44,6 +44,7 @@ void add_reg(XUnit &u, int in_lo, int n_in, int interleaved) {
 XUnit empty_unit() {
   XUnit u;
   std::memset(&u, 0, sizeof(u));
+  u.n_chan = 1;
   return u;
 }
 
@@ -56,7 +57,22 @@ std::vector<XUnit> build_schedule(int N, int cover) {
   std::vector<XUnit> units;
   const int n16 = round_up(N, 16);
   const int n_rt = (N + kTileInputs - 1) / kTileInputs;
-  if (N <= 256 && cover == kCoverWindow) {
+  if (N <= kTileInputs && cover == kCoverWindow) {
+    // one row tile: a unit covers two channels (two staged regions, two
+    // accumulators), so every chunk handed from the unpack to the MMA
+    // issuers carries twice the work
+    XUnit u = empty_unit();
+    u.n_chan = 2;
+    for (int r = 0; r < 2; ++r) {
+      add_reg(u, 0, kTileInputs, 1);
+      u.reg[r].chan_off = r;
+    }
+    for (int r = 0; r < 2; ++r) {
+      add_seg(u, u.reg[r].z_row, u.reg[r].z_row, 2048, n16, 0, 0);
+      u.seg[r].chan_off = r;
+    }
+    units.push_back(u);
+  } else if (N <= 256 && cover == kCoverWindow) {
     std::vector<int> tiles(n_rt);
     for (int t = 0; t < n_rt; ++t) tiles[t] = n_rt - 1 - t;  // largest strip first
     std::vector<std::vector<int>> bins;
@@ -200,7 +216,7 @@ int build_items(const std::vector<ProbWork> &probs, int grid, std::vector<XItem>
     pw[p].npk = pw[p].ppb * pr.n_blocks;
     pw[p].nseg = (pw[p].npk + max_item_pk - 1) / max_item_pk;
     for (const XUnit &u : *pr.units)
-      total += (long long)pr.n_chan *
+      total += (long long)((pr.n_chan + u.n_chan - 1) / u.n_chan) *
                ((long long)pw[p].cpb * pr.n_blocks * u.z_rows + kFold * u.work * pw[p].nseg);
   }
   if (total == 0 || grid <= 0) {
@@ -278,7 +294,7 @@ int build_items(const std::vector<ProbWork> &probs, int grid, std::vector<XItem>
     const long long npk_total = pw[p].npk;
     const int nseg = pw[p].nseg;
     for (int t = 0; t < (int)probs[p].units->size(); ++t)
-      for (int c = 0; c < probs[p].n_chan; ++c)
+      for (int c = 0; c < probs[p].n_chan; c += std::max(1, (*probs[p].units)[t].n_chan))
         // fold-window segment sg: stages [npk sg / nseg, npk (sg + 1) / nseg)
         for (int sg = 0; sg < nseg; ++sg)
           deal(p, t, c, (int)(npk_total * sg / nseg), (int)(npk_total * (sg + 1) / nseg));

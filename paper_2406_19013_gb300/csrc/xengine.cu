@@ -167,13 +167,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t dst0 = smem_u32(pk_buf + (size_t)s * p.pk_stage_bytes);
           for (int r = 0; r < n_reg; ++r) {
             const int in_lo = u->reg[r].in_lo, n_in = u->reg[r].n_in, off = u->reg[r].pk_off;
+            const int ch = item.chan + u->reg[r].chan_off;  // past the last: zero fill
             for (int bx = 0; bx < n_in; bx += kTileInputs) {
               if (TCN)  // (input, channel, time): a [128 samples][64 inputs] box
-                tma_load_3d(dst0 + off + bx * kPackedRowBytes, tmap, full, in_lo + bx, item.chan,
+                tma_load_3d(dst0 + off + bx * kPackedRowBytes, tmap, full, in_lo + bx, ch,
                             kc * kPkSamples);
               else        // (time, input, channel): a [64 inputs][128 samples] box
                 tma_load_3d(dst0 + off + bx * kPackedRowBytes, tmap, full, kc * kPkSamples,
-                            in_lo + bx, item.chan);
+                            in_lo + bx, ch);
             }
           }
           if (++s == p.pk_stages) { s = 0; ph ^= 1u; }
@@ -393,7 +394,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       const XItem item = item_at(p, it);
       const XProb pb = p.probs[item.prob];
       const XUnit *u = pb.units + item.tpl;
-      const int c = item.chan;
       if (!mbar_wait(b.acc_full, (uint32_t)(nu & 1), abort_flag, to)) break;
       // once the kernel is winding down nothing more is folded: the
       // integration is void and is reported as such
@@ -407,6 +407,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int l_in = TCN ? ((l - (g & 3)) & 7) : l;
       for (int sg = 0; sg < n_seg; ++sg) {
         const XSeg sgm = u->seg[sg];
+        const int c = item.chan + sgm.chan_off;
+        if (c >= pb.n_chan) continue;  // a two-channel unit's missing last channel
         const int i = sgm.row_in0 + 8 * g + l_in;
         const bool row_ok = i < pb.n_in;
         int64_t *arow = pb.acc + ((long long)c * pb.n_pairs + (long long)i * (i + 1) / 2) * 2;
