@@ -276,18 +276,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       const XProb pb = p.probs[item.prob];
       const XUnit *u = pb.units + item.tpl;
       const int n_reg = u->n_reg;
-      // per-region constants of this thread (at most two regions)
+      // per-region constants of this thread (at most two regions).  When
+      // both regions together have at most R rows (a two-channel unit),
+      // region 1's rows follow region 0's in the thread mapping, so every
+      // unpack warp gets work; otherwise both start at row0.
+      const int pack =
+          n_reg == 2 && u->reg[0].n_in + u->reg[1].n_in <= R ? u->reg[0].n_in : 0;
       uint32_t src_off[2], dst_off[2], dst_step[2];
       int n_k[2], il[2];
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         const XRegion rg = u->reg[r < n_reg ? r : 0];
+        const int rr = r == 1 ? row0 - pack : row0;  // this thread's row of the region
         il[r] = rg.interleaved;
-        const int rho0 = rg.interleaved ? (((row0 >> 3) << 4) | sw) : row0;
-        src_off[r] = (uint32_t)(rg.pk_off + row0 * kPackedRowBytes);
+        const int rho0 = rg.interleaved ? (((rr >> 3) << 4) | sw) : rr;
+        src_off[r] = (uint32_t)(rg.pk_off + rr * kPackedRowBytes);
         dst_off[r] = (uint32_t)(rg.z_row + rho0) * 128u;
         dst_step[r] = (uint32_t)((rg.interleaved ? 2 * R : R) * 128);  // R rows further on
-        n_k[r] = r < n_reg && row0 < rg.n_in ? (rg.n_in - row0 + R - 1) / R : 0;
+        n_k[r] = r < n_reg && rr >= 0 && rr < rg.n_in ? (rg.n_in - rr + R - 1) / R : 0;
       }
       for (int k = item.pk0; k < item.pk0 + item.npk && ok; ++k) {
         const int nch = chunks_in_pk(pb, k % pb.pk_per_block);
