@@ -60,6 +60,28 @@ def set_channels(n_chan: int):
     WORKLOAD = WORKLOAD.replace("1024 channels", f"{n_chan} channels (profiling size)")
 
 
+def set_antennas(n_ant: int):
+    """Profiling only: another array size than the paper's 96 dual-pol antennas
+    (the same seeded noise-plus-tone recipe)."""
+    global N_ANT, N_IN, N_PAIRS, N_APAIRS, CMAC_PER_BLOCK, WORKLOAD
+    N_ANT = n_ant
+    N_IN = N_ANT * N_POL
+    N_PAIRS = N_IN * (N_IN + 1) // 2
+    N_APAIRS = N_ANT * (N_ANT + 1) // 2
+    CMAC_PER_BLOCK = N_PAIRS * N_CHAN * BLOCK_LEN
+    WORKLOAD = WORKLOAD.replace("96 dual-pol antennas (192 inputs, 18528 pairs with autos)",
+                                f"{n_ant} dual-pol antennas ({N_IN} inputs, profiling size)")
+
+
+def paper_like_workload(seed: int = 1):
+    """The paper workload's recipe at the (possibly profiling) input count."""
+    from synth import synth
+    if N_IN == 192:
+        return synth.workload("paper", seed=seed)
+    return synth.Workload("paper", N_ANT, N_POL, 1024, BLOCK_LEN, BLOCKS_PER_STEP, seed,
+                          synth.random_phase_tone(N_IN, seed))
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -93,16 +115,19 @@ def fp8_peak():
     if _FP8_PEAK is None:
         from paper_2406_19013_gb300.corr import mma_rate
         best = None
-        for issuers, tm in ((1, False), (2, False), (1, True)):
-            tf, ms, cyc = mma_rate(n=256, issuers=issuers, iters=20000, a_from_tmem=tm, reps=3)
+        # the shapes that came out fastest in the full sweep (--workload mma_peak)
+        for n, issuers, tm in ((256, 1, False), (256, 2, False), (256, 1, True), (128, 3, True)):
+            tf, ms, cyc = mma_rate(n=n, issuers=issuers, iters=20000 * 256 // (n * issuers),
+                                   a_from_tmem=tm, reps=3)
             if best is None or tf > best[0]:
-                best = (tf, ms, cyc, issuers, tm)
-        tf, ms, cyc, issuers, tm = best
+                best = (tf, ms, cyc, n, issuers, tm)
+        tf, ms, cyc, n, issuers, tm = best
         bx2, kind = bf16_x2_peak()
-        _FP8_PEAK = (tf, f"measured in this run: dense E5M2 tcgen05.mma M=128 N=256 K=32, "
+        _FP8_PEAK = (tf, f"measured in this run: dense E5M2 tcgen05.mma M=128 N={n} K=32, "
                          f"{issuers} issuing thread(s) per SM, A from {'TMEM' if tm else 'smem'}, "
-                         f"{ms:.2f} ms launches, {cyc:.0f} cycles per MMA (corr_mma_rate); "
-                         f"{kind} bf16 burst x {FP8_OVER_BF16:g} = {bx2:.0f} TFLOP/s for context")
+                         f"{ms:.2f} ms launches, {cyc:.0f} cycles per MMA per issuer "
+                         f"(corr_mma_rate); {kind} bf16 burst x {FP8_OVER_BF16:g} = {bx2:.0f} "
+                         f"TFLOP/s for context")
     return _FP8_PEAK
 
 
@@ -241,7 +266,7 @@ def run_ours(args):
 
     # ---- inputs: a ring of distinct blocks, generated on the host in pinned
     # memory; rank r holds channels [r*1024, (r+1)*1024) of one global band
-    w = synth.workload("paper", seed=1)
+    w = paper_like_workload(seed=1)
     c0, n_band = shard.band(rank, ws, N_CHAN * ws)
     assert n_band == N_CHAN
     ring_n = max(1, args.ring)
@@ -486,6 +511,44 @@ def run_large_n(args):
     return 0
 
 
+def run_mma_peak(args):
+    """The dense E5M2 tcgen05.mma rate by shape (corr_mma_rate): N = 64..256,
+    one to four issuing threads per SM, operands in shared memory or A in
+    TMEM.  The best of these is the roofline peak of the CMAC kernel."""
+    import torch
+
+    from paper_2406_19013_gb300 import build
+    from paper_2406_19013_gb300.corr import mma_rate
+
+    torch.cuda.set_device(0)
+    build.build()
+    rows = []
+    for tm in (False, True):
+        for n in (64, 128, 192, 256):
+            for iss in (1, 2, 3, 4):
+                if iss * n + (32 if tm else 0) > 512:
+                    continue
+                iters = max(100, int(20000 * 256 / n / iss))
+                tf, ms, cyc = mma_rate(n=n, issuers=iss, iters=iters, a_from_tmem=tm, reps=2)
+                rows.append({"a": "tmem" if tm else "smem", "n": n, "issuers": iss,
+                             "tflops": round(tf, 1), "ms": round(ms, 3),
+                             "cycles_per_mma_per_issuer": round(cyc, 1)})
+    best = max(rows, key=lambda r: r["tflops"])
+    bx2, kind = bf16_x2_peak()
+    line = {
+        "metric": "dense E5M2 tcgen05.mma TFLOP/s (M=128, K=32, fp32 accumulation)",
+        "value": best["tflops"], "unit": "TFLOP/s", "n_gpus": 1, "steps": 2, "warmup": 1,
+        "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "e5m2", "data": "synthetic",
+        "config": {"workload": "one CTA per SM issuing back-to-back MMAs on 128B-swizzled "
+                               "operand tiles of random E5M2 values in [-7, 7]",
+                   "best": best, "bf16_burst_x2_tflops": bx2, "bf16_source": kind},
+        "sweep": rows,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batched(args):
     """A batch of 64 independent correlators (input counts 32..512, 16..1024
     channels, 256..16384-sample blocks) integrated by corr_batch_push, against
@@ -606,7 +669,7 @@ def run_corner_turn(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     build.build()
-    w = synth.workload("paper", seed=1)
+    w = paper_like_workload(seed=1)
     hb = torch.empty((N_CHAN, N_IN, BLOCK_LEN), dtype=torch.uint8, pin_memory=True)
     w.block(0, n_chan=N_CHAN, out=hb.numpy())
     x = hb.to(dev)
@@ -648,8 +711,8 @@ def run_corner_turn(args):
         "unit": "GB/s", "n_gpus": 1, "steps": 4 * k, "warmup": args.warmup,
         "ms_per_step": ms_turn, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": f"uint8 [8192][{N_CHAN}][192] (F-engine order) -> "
-                               f"[{N_CHAN}][192][8192]",
+        "config": {"workload": f"uint8 [8192][{N_CHAN}][{N_IN}] (F-engine order) -> "
+                               f"[{N_CHAN}][{N_IN}][8192]",
                    "bytes_per_step": nbytes, "l2": "inputs larger than L2 (1.61 GB)"},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                      "frac": gbs / hbm, "peak_source": f"{hbm_kind} copy bandwidth",
@@ -896,7 +959,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-channels", type=int, default=16)
     ap.add_argument("--workload", choices=["paper", "large_n", "batched", "corner_turn",
-                                           "served", "fengine"],
+                                           "served", "fengine", "mma_peak"],
                     default="paper",
                     help="paper: the 192-input integration (default); large_n: 2048 inputs, "
                          "256 channels, 16 x 4096-sample blocks; batched: 64 mixed "
@@ -907,7 +970,12 @@ def main():
                     help="fengine workload: spectra per input (profiling a smaller run)")
     ap.add_argument("--n-chan", type=int, default=N_CHAN,
                     help="channels per GPU (profiling a smaller band; the reported workload is 1024)")
+    ap.add_argument("--n-ant", type=int, default=N_ANT,
+                    help="dual-pol antennas (profiling another array size; the reported workload "
+                         "is 96)")
     args = ap.parse_args()
+    if args.n_ant != N_ANT:
+        set_antennas(args.n_ant)
     if args.n_chan != N_CHAN:
         set_channels(args.n_chan)
     if args.warmup < 3:
@@ -917,6 +985,8 @@ def main():
         return run_reference(args)
     if args.workload == "large_n":
         return run_large_n(args)
+    if args.workload == "mma_peak":
+        return run_mma_peak(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "corner_turn":

@@ -9,10 +9,10 @@
 // [a, b] (used on both sides) and a "Q row" [b, -a] (row side only).  That is
 // a dense rank-2T update, so it runs on the tensor cores: 8-bit float operands
 // (E5M2: every integer in [-8, 8] is exact) and fp32 accumulators in TMEM.
-// Each product is an integer of magnitude <= 64 and the partial sums of a
-// launch stay below 128 * (samples per launch) < 2^24, so every fp32
-// accumulation is exact; the
-// partials are folded into the int64 integration buffer once per launch.
+// Each product is an integer of magnitude <= 64 and an item never spans more
+// than 131071 samples, so its partial sums stay below 128 * 131071 < 2^24 and
+// every fp32 accumulation is exact; each item's partials are folded into the
+// int64 integration buffer when it ends.
 //
 // Kernel structure (persistent, one CTA per SM, 25 warps):
 //   warp 20     TMA producer: packed bytes [channel][input][time] -> smem ring
@@ -22,11 +22,12 @@
 //   warps 21-24 MMA issuers: tcgen05.mma M=128 (64 inputs' A rows + Q rows),
 //               N = columns of the triangle strip, K = 32 per instruction;
 //               one issuing thread per accumulator, because a single thread
-//               issues an MMA only every ~200 cycles whatever its size
+//               issues an MMA only every ~110-126 cycles in a loop with
+//               waits and commits, too slow for the N = 64 strips alone
 //   warps 16-19 epilogue: tcgen05.ld of the fp32 accumulators, exchange of
 //               re/im between lanes, int64 red.add into the lower triangle
-// A launch integrates up to kMaxBlocksPerLaunch blocks before the fold, as
-// long as the samples per fold keep every fp32 partial below 2^24.
+// A launch integrates up to kMaxBlocksPerLaunch blocks; the host cuts its
+// items at fold windows of at most 131071 samples.
 // A work unit is (problem, template, channel); a template names the inputs
 // staged per chunk and the MMAs (row tile x column range) that cover its part
 // of the triangle.  The host cuts the units into items (a unit over a range
