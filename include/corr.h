@@ -58,6 +58,7 @@ extern "C" {
 #define CORR_EARCH (-4)    /* current device is not compute capability 10.3 */
 #define CORR_ETIMEOUT (-5) /* a device-side wait ran out; results are void */
 #define CORR_ESTATE (-6)   /* call not valid in the context's current state */
+#define CORR_EBOUNDS (-7)  /* debug builds: an address check or a guard band failed */
 
 /* Largest block_len accepted (Sec. 2.4's integrations are blocks of many
  * samples; 2^24 - 1 bounds the host-side sample counters of one block). */
@@ -295,6 +296,65 @@ int corr_selftest_timeout(corr_ctx *ctx, const uint8_t *d_block, int timeout_ms,
 
 /* Number of kernel launches the context has enqueued (pushes and dumps). */
 long long corr_launch_count(const corr_ctx *ctx);
+
+/*
+ * Counters of a context, kept on the host as calls are enqueued (nothing is
+ * read from the device).  An integration (Sec. 2.4) is the blocks pushed
+ * between two dumps.
+ */
+typedef struct corr_stats {
+  long long blocks_pushed;   /* blocks integrated since corr_create */
+  long long samples_total;   /* samples per input integrated since corr_create */
+  long long samples_pending; /* samples per input in the integration in progress */
+  long long dumps;           /* completed corr_dump / corr_dump_host calls */
+  long long launches;        /* kernel launches enqueued (as corr_launch_count) */
+} corr_stats;
+
+/* Fills *out.  Errors: CORR_EINVAL (ctx or out NULL). */
+int corr_get_stats(const corr_ctx *ctx, corr_stats *out);
+
+/*
+ * Checkpoint of the integration in progress.  The accumulators are integers,
+ * so an integration resumed from a snapshot ends bit-identical to one that
+ * never stopped.
+ *
+ * corr_snapshot waits for `stream`, then copies the int64 accumulators to
+ * h_acc (caller-owned host memory of vis_elems int64, the layout of
+ * corr_dump's visibilities: [n_chan][P][2]) and the integration's sample count
+ * to *samples.  The context is unchanged.
+ *
+ * corr_restore replaces the integration in progress of `ctx` with a snapshot
+ * taken from a context of the same shape (this one or another, in this
+ * process or an earlier one): it copies h_acc to the accumulators on `stream`,
+ * waits for the copy, and sets the integration's sample count to `samples`.
+ *
+ * Errors: CORR_EINVAL (NULL pointers, samples < 0), CORR_ECUDA.
+ */
+int corr_snapshot(corr_ctx *ctx, int64_t *h_acc, long long *samples, void *stream);
+int corr_restore(corr_ctx *ctx, const int64_t *h_acc, long long samples, void *stream);
+
+/*
+ * Debug builds.  Compiling the library with CORR_DEBUG defined (the Python
+ * build's debug variant, libcorr_debug.so) adds checks that cost time and
+ * change no result:
+ *   - every int64 atomic add of the CMAC kernels' fold and every element the
+ *     dump touches is checked against its integration buffer; an address
+ *     outside it is skipped and recorded;
+ *   - a context's integration buffer gets a guard band of 4096 bytes on each
+ *     side, filled with 0xA5 at creation; corr_check compares both bands with
+ *     the pattern before it reads the status word.
+ * A recorded failure makes the next corr_check (corr_batch_check for the
+ * address checks of a batch) return CORR_EBOUNDS, which takes precedence over
+ * CORR_ETIMEOUT.  Release builds carry none of this code.
+ *
+ * corr_debug_build returns 1 in a debug build, else 0.
+ * corr_debug_corrupt_guard overwrites one byte in the middle of the guard
+ * band before (side 0) or after (side 1) the integration buffer, from the
+ * host, so that a test can see corr_check report it.  Errors: CORR_EINVAL,
+ * CORR_ESTATE (release build), CORR_ECUDA.
+ */
+int corr_debug_build(void);
+int corr_debug_corrupt_guard(corr_ctx *ctx, int side);
 
 /*
  * Batches: many independent correlators in shared launches.

@@ -15,7 +15,10 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libcorr.so")
+# CORR_LIB_VARIANT=debug loads the debug build (libcorr_debug.so: address
+# checks in the kernels, guard bands around the integration buffers).
+LIB_PATH = os.path.join(_HERE, "libcorr_debug.so" if os.environ.get("CORR_LIB_VARIANT") == "debug"
+                        else "libcorr.so")
 
 CORR_OK = 0
 CORR_EINVAL = -1
@@ -24,6 +27,7 @@ CORR_ECUDA = -3
 CORR_EARCH = -4
 CORR_ETIMEOUT = -5
 CORR_ESTATE = -6
+CORR_EBOUNDS = -7
 CORR_MAX_BLOCK_LEN = 16777215
 CORR_FOLD_SAMPLES = 131071
 CORR_STATIC_MAX_BLOCK_LEN = 131056
@@ -66,9 +70,24 @@ ABI = [
     ("corr_xcorr_static", _ci, [_vp, _ci, _ci, _ci, _ci, _vp, _vp]),
     ("corr_mma_rate", _ci, [_ci, _ci, _ci, _ci, _vp, _vp, _vp]),
     ("corr_launch_count", _ll, [_vp]),
+    ("corr_get_stats", _ci, [_vp, _vp]),
+    ("corr_snapshot", _ci, [_vp, _vp, ctypes.POINTER(_ll), _vp]),
+    ("corr_restore", _ci, [_vp, _vp, _ll, _vp]),
+    ("corr_debug_build", _ci, []),
+    ("corr_debug_corrupt_guard", _ci, [_vp, _ci]),
     ("corr_destroy", None, [_vp]),
     ("corr_strerror", ctypes.c_char_p, [_ci]),
 ]
+
+class Stats(ctypes.Structure):
+    _fields_ = [("blocks_pushed", _ll), ("samples_total", _ll), ("samples_pending", _ll),
+                ("dumps", _ll), ("launches", _ll)]
+
+
+def debug_build() -> bool:
+    """Whether the loaded library is the debug build."""
+    return bool(load().corr_debug_build())
+
 
 class ArrayDesc(ctypes.Structure):
     _fields_ = [("n_ant", ctypes.c_int), ("n_pol", ctypes.c_int), ("n_chan", ctypes.c_int),
@@ -384,6 +403,31 @@ class Correlator:
 
     def launch_count(self) -> int:
         return int(self._lib.corr_launch_count(self._h))
+
+    def stats(self) -> dict:
+        """The context's counters (corr_get_stats)."""
+        st = Stats()
+        _ck(self._lib.corr_get_stats(self._h, ctypes.byref(st)), "corr_get_stats")
+        return {name: int(getattr(st, name)) for name, _ in Stats._fields_}
+
+    def snapshot(self, stream=None):
+        """(acc int64[n_chan][P][2] numpy array, samples): the integration in
+        progress, for corr_restore."""
+        acc = np.empty((self.n_chan, self.n_pairs, 2), dtype=np.int64)
+        n = _ll()
+        _ck(self._lib.corr_snapshot(self._h, acc.ctypes.data, ctypes.byref(n),
+                                    _stream_handle(stream)), "corr_snapshot")
+        return acc, n.value
+
+    def restore(self, acc, samples: int, stream=None):
+        """Replaces the integration in progress with a snapshot."""
+        pa = self._host_ptr(acc, np.int64, self.n_chan * self.n_pairs * 2, "acc")
+        _ck(self._lib.corr_restore(self._h, pa, int(samples), _stream_handle(stream)),
+            "corr_restore")
+
+    def debug_corrupt_guard(self, side: int):
+        """Debug builds: overwrites a byte of a guard band (corr_debug_corrupt_guard)."""
+        _ck(self._lib.corr_debug_corrupt_guard(self._h, side), "corr_debug_corrupt_guard")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -24,6 +24,7 @@
 #include "corr.h"
 #include "xe_sched.h"
 #include "xe_internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -300,6 +301,7 @@ extern "C" {
 
 int corr_batch_create(int n_inst, const int *n_ant, const int *n_pol, const int *n_chan,
                       const int *block_len, int flags, corr_batch **out) {
+  CORR_TRACE("corr_batch_create");
   if (!out) return CORR_EINVAL;
   *out = nullptr;
   if (n_inst <= 0 || !n_ant || !n_pol || !n_chan || !block_len) return CORR_EINVAL;
@@ -451,6 +453,7 @@ int corr_batch_create(int n_inst, const int *n_ant, const int *n_pol, const int 
 }
 
 int corr_batch_push(corr_batch *b, const uint8_t *const *d_blocks, void *stream) {
+  CORR_TRACE("corr_batch_push");
   if (!b || !d_blocks) return CORR_EINVAL;
   for (size_t k = 0; k < b->inst.size(); ++k)
     if (!d_blocks[k] || (reinterpret_cast<uintptr_t>(d_blocks[k]) & 15u) != 0) return CORR_EINVAL;
@@ -502,13 +505,15 @@ int corr_batch_push(corr_batch *b, const uint8_t *const *d_blocks, void *stream)
 }
 
 int corr_batch_dump(corr_batch *b, int inst, int64_t *d_vis, int64_t *d_stokes, void *stream) {
+  CORR_TRACE("corr_batch_dump");
   if (!b || inst < 0 || inst >= (int)b->inst.size()) return CORR_EINVAL;
   BInst &in = b->inst[inst];
   if (d_stokes && in.n_pol != 2) return CORR_EINVAL;
   if ((reinterpret_cast<uintptr_t>(d_vis) & 15u) || (reinterpret_cast<uintptr_t>(d_stokes) & 15u))
     return CORR_EINVAL;
   int rc = cuda_err(xe::launch_dump(b->d_acc + in.acc_off, d_vis, d_stokes, in.n_ant, in.n_pol,
-                                    in.n_chan, static_cast<cudaStream_t>(stream), b->n_sm * 8));
+                                    in.n_chan, static_cast<cudaStream_t>(stream), b->n_sm * 8,
+                                    b->d_status));
   if (rc != CORR_OK) return rc;
   b->launches++;
   in.samples = 0;
@@ -544,7 +549,7 @@ int corr_batch_check(corr_batch *b, void *stream) {
     return rc;
   if (status) {
     if ((rc = cuda_err(cudaMemset(b->d_status, 0, sizeof(int)))) != CORR_OK) return rc;
-    return CORR_ETIMEOUT;
+    return (status & xe::kStatusBounds) ? CORR_EBOUNDS : CORR_ETIMEOUT;
   }
   return CORR_OK;
 }

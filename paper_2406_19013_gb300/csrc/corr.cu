@@ -13,6 +13,7 @@
 #include "corr.h"
 #include "xe_sched.h"
 #include "xe_internal.h"
+#include "trace.h"
 
 using xe::XParams;
 using xe::XSeg;
@@ -31,6 +32,7 @@ struct corr_ctx {
   long long n_pairs, n_apairs;
   int device, n_sm;
   int64_t *d_acc;
+  unsigned char *acc_alloc;  // the allocation holding d_acc (with guard bands in debug builds)
   int *d_status;
   XUnit *d_units;
   xe::XProb *d_prob;
@@ -43,8 +45,9 @@ struct corr_ctx {
   int pitch;           // row pitch of the staged block (block_len rounded up to 16)
   uint8_t *d_pitched;  // [n_chan][n_in][pitch] when block_len % 16 != 0
   uint8_t *d_turned;   // [n_chan][n_in][pitch]: corner-turned blocks (allocated on first use)
-  long long samples;
+  long long samples;        // samples per input in the integration in progress
   long long launches;
+  long long blocks_pushed, samples_total, dumps;
   unsigned long long timeout_ns;
   // host-buffer variants
   uint8_t *d_stage[2];
@@ -55,6 +58,12 @@ struct corr_ctx {
 };
 
 namespace {
+
+#ifdef CORR_DEBUG
+constexpr bool kDebug = true;
+#else
+constexpr bool kDebug = false;
+#endif
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
@@ -72,7 +81,7 @@ int encode_block_map(const corr_ctx *ctx, const void *base, CUtensorMap *m) {
 
 int free_ctx(corr_ctx *ctx) {
   if (!ctx) return CORR_OK;
-  cudaFree(ctx->d_acc);
+  cudaFree(ctx->acc_alloc);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_units);
   cudaFree(ctx->d_prob);
@@ -160,11 +169,13 @@ const char *corr_strerror(int code) {
     case CORR_EARCH: return "device is not compute capability 10.3 (sm_103)";
     case CORR_ETIMEOUT: return "a device-side wait timed out";
     case CORR_ESTATE: return "call not valid in the current state";
+    case CORR_EBOUNDS: return "an address check or a guard band failed (debug build)";
     default: return "unknown error";
   }
 }
 
 int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out) {
+  CORR_TRACE("corr_create");
   if (!out) return CORR_EINVAL;
   *out = nullptr;
   if (n_ant <= 0 || n_chan <= 0 || block_len <= 0 || (n_pol != 1 && n_pol != 2))
@@ -238,9 +249,19 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
 
   int rc = CORR_OK;
   const size_t acc_bytes = (size_t)n_chan * (size_t)ctx->n_pairs * 16;
-  if ((rc = cuda_err(cudaMalloc(&ctx->d_acc, acc_bytes))) != CORR_OK ||
+  // debug builds put a guard band of kGuardBytes on each side of the
+  // integration buffer; corr_check verifies them
+  const size_t guard = kDebug ? xe::kGuardBytes : 0;
+  if ((rc = cuda_err(cudaMalloc(&ctx->acc_alloc, acc_bytes + 2 * guard))) != CORR_OK ||
       (rc = cuda_err(cudaMalloc(&ctx->d_status, sizeof(int)))) != CORR_OK ||
       (rc = cuda_err(cudaMalloc(&ctx->d_units, units.size() * sizeof(XUnit)))) != CORR_OK) {
+    free_ctx(ctx);
+    return rc;
+  }
+  ctx->d_acc = reinterpret_cast<int64_t *>(ctx->acc_alloc + guard);
+  if (guard && ((rc = cuda_err(cudaMemset(ctx->acc_alloc, xe::kGuardByte, guard))) != CORR_OK ||
+                (rc = cuda_err(cudaMemset(ctx->acc_alloc + guard + acc_bytes, xe::kGuardByte,
+                                          guard))) != CORR_OK)) {
     free_ctx(ctx);
     return rc;
   }
@@ -335,7 +356,11 @@ int launch_staged(corr_ctx *ctx, const uint8_t *const *staged, int nb, cudaStrea
                             : xe::launch_cmac(maps, p, pl.grid, ctx->smem_bytes, st))) != CORR_OK)
     return rc;
   ctx->launches++;
-  if (!selftest_timeout_ns) ctx->samples += (long long)nb * ctx->block_len;
+  if (!selftest_timeout_ns) {
+    ctx->samples += (long long)nb * ctx->block_len;
+    ctx->samples_total += (long long)nb * ctx->block_len;
+    ctx->blocks_pushed += nb;
+  }
   return CORR_OK;
 }
 
@@ -345,6 +370,7 @@ extern "C" {
 
 int corr_push_blocks(corr_ctx *ctx, const uint8_t *const *d_blocks, int n_blocks,
                      void *stream) {
+  CORR_TRACE("corr_push_blocks");
   if (!ctx || !d_blocks || n_blocks <= 0) return CORR_EINVAL;
   for (int k = 0; k < n_blocks; ++k)
     if (!d_blocks[k] || (reinterpret_cast<uintptr_t>(d_blocks[k]) & 15u) != 0) return CORR_EINVAL;
@@ -373,6 +399,7 @@ int corr_push_blocks(corr_ctx *ctx, const uint8_t *const *d_blocks, int n_blocks
 
 int corr_corner_turn(const uint8_t *d_src, uint8_t *d_dst, int n_in, int n_chan, int block_len,
                      void *stream) {
+  CORR_TRACE("corr_corner_turn");
   if (!d_src || !d_dst || n_in <= 0 || n_chan <= 0 || block_len <= 0) return CORR_EINVAL;
   if ((reinterpret_cast<uintptr_t>(d_src) & 3u) || (reinterpret_cast<uintptr_t>(d_dst) & 3u))
     return CORR_EINVAL;
@@ -403,6 +430,7 @@ int corr_selftest_timeout(corr_ctx *ctx, const uint8_t *d_block, int timeout_ms,
 }
 
 int corr_push_block_tcn(corr_ctx *ctx, const uint8_t *d_src, void *stream) {
+  CORR_TRACE("corr_push_block_tcn");
   if (!ctx || !d_src || (reinterpret_cast<uintptr_t>(d_src) & 3u)) return CORR_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // The shared-memory kernel stages F-engine-order blocks directly (TMA boxes
@@ -430,20 +458,23 @@ int corr_push_block(corr_ctx *ctx, const uint8_t *d_block, void *stream) {
 }
 
 int corr_dump(corr_ctx *ctx, int64_t *d_vis, int64_t *d_stokes, void *stream) {
+  CORR_TRACE("corr_dump");
   if (!ctx) return CORR_EINVAL;
   if (d_stokes && ctx->n_pol != 2) return CORR_EINVAL;
   if ((reinterpret_cast<uintptr_t>(d_vis) & 15u) || (reinterpret_cast<uintptr_t>(d_stokes) & 15u))
     return CORR_EINVAL;
   int rc = cuda_err(xe::launch_dump(ctx->d_acc, d_vis, d_stokes, ctx->n_ant, ctx->n_pol,
                                     ctx->n_chan, static_cast<cudaStream_t>(stream),
-                                    ctx->n_sm * 8));
+                                    ctx->n_sm * 8, ctx->d_status));
   if (rc != CORR_OK) return rc;
   ctx->launches++;
+  ctx->dumps++;
   ctx->samples = 0;
   return CORR_OK;
 }
 
 int corr_push_block_host(corr_ctx *ctx, const uint8_t *h_block, void *stream) {
+  CORR_TRACE("corr_push_block_host");
   if (!ctx || !h_block) return CORR_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t nb = block_bytes(ctx);
@@ -477,6 +508,7 @@ int corr_push_block_host(corr_ctx *ctx, const uint8_t *h_block, void *stream) {
 }
 
 int corr_dump_host(corr_ctx *ctx, int64_t *h_vis, int64_t *h_stokes, void *stream) {
+  CORR_TRACE("corr_dump_host");
   if (!ctx) return CORR_EINVAL;
   if (h_stokes && ctx->n_pol != 2) return CORR_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -510,8 +542,17 @@ int corr_sizes(const corr_ctx *ctx, size_t *vis_elems, size_t *stokes_elems,
 }
 
 int corr_check(corr_ctx *ctx, void *stream) {
+  CORR_TRACE("corr_check");
   if (!ctx) return CORR_EINVAL;
   int rc;
+  if (kDebug) {
+    const size_t acc_bytes = (size_t)ctx->n_chan * ctx->n_pairs * 16;
+    if ((rc = cuda_err(xe::launch_guard_check(ctx->acc_alloc,
+                                              ctx->acc_alloc + xe::kGuardBytes + acc_bytes,
+                                              xe::kGuardBytes, ctx->d_status,
+                                              static_cast<cudaStream_t>(stream)))) != CORR_OK)
+      return rc;
+  }
   if ((rc = cuda_err(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)))) != CORR_OK)
     return rc;
   int status = 0;
@@ -520,7 +561,7 @@ int corr_check(corr_ctx *ctx, void *stream) {
     return rc;
   if (status) {
     if ((rc = cuda_err(cudaMemset(ctx->d_status, 0, sizeof(int)))) != CORR_OK) return rc;
-    return CORR_ETIMEOUT;
+    return (status & xe::kStatusBounds) ? CORR_EBOUNDS : CORR_ETIMEOUT;
   }
   return CORR_OK;
 }
@@ -590,6 +631,55 @@ int corr_plan_cover(int n_in, int cover_kind, uint8_t *cover, int *n_units,
 }
 
 long long corr_launch_count(const corr_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int corr_debug_build(void) { return kDebug ? 1 : 0; }
+
+int corr_debug_corrupt_guard(corr_ctx *ctx, int side) {
+  if (!ctx || (side != 0 && side != 1)) return CORR_EINVAL;
+  if (!kDebug) return CORR_ESTATE;
+  const size_t acc_bytes = (size_t)ctx->n_chan * ctx->n_pairs * 16;
+  unsigned char *at = side == 0 ? ctx->acc_alloc + xe::kGuardBytes / 2
+                                : ctx->acc_alloc + xe::kGuardBytes + acc_bytes + xe::kGuardBytes / 2;
+  return cuda_err(cudaMemset(at, 0, 1));
+}
+
+int corr_get_stats(const corr_ctx *ctx, corr_stats *out) {
+  if (!ctx || !out) return CORR_EINVAL;
+  out->blocks_pushed = ctx->blocks_pushed;
+  out->samples_total = ctx->samples_total;
+  out->samples_pending = ctx->samples;
+  out->dumps = ctx->dumps;
+  out->launches = ctx->launches;
+  return CORR_OK;
+}
+
+int corr_snapshot(corr_ctx *ctx, int64_t *h_acc, long long *samples, void *stream) {
+  if (!ctx || !h_acc || !samples) return CORR_EINVAL;
+  CORR_TRACE("corr_snapshot");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)ctx->n_chan * ctx->n_pairs * 16;
+  int rc;
+  if ((rc = cuda_err(cudaMemcpyAsync(h_acc, ctx->d_acc, bytes, cudaMemcpyDeviceToHost, st))) !=
+          CORR_OK ||
+      (rc = cuda_err(cudaStreamSynchronize(st))) != CORR_OK)
+    return rc;
+  *samples = ctx->samples;
+  return CORR_OK;
+}
+
+int corr_restore(corr_ctx *ctx, const int64_t *h_acc, long long samples, void *stream) {
+  if (!ctx || !h_acc || samples < 0) return CORR_EINVAL;
+  CORR_TRACE("corr_restore");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)ctx->n_chan * ctx->n_pairs * 16;
+  int rc;
+  if ((rc = cuda_err(cudaMemcpyAsync(ctx->d_acc, h_acc, bytes, cudaMemcpyHostToDevice, st))) !=
+          CORR_OK ||
+      (rc = cuda_err(cudaStreamSynchronize(st))) != CORR_OK)
+    return rc;
+  ctx->samples = samples;
+  return CORR_OK;
+}
 
 void corr_destroy(corr_ctx *ctx) { free_ctx(ctx); }
 

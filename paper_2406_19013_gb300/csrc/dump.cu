@@ -28,7 +28,8 @@ __device__ __forceinline__ long long tri_row(long long a) {
 }
 
 __global__ void dump_dual_kernel(int64_t *__restrict__ acc, int64_t *__restrict__ vis,
-                                 int64_t *__restrict__ stokes, int n_ant, int n_chan) {
+                                 int64_t *__restrict__ stokes, int n_ant, int n_chan,
+                                 int *status) {
   const long long n_in = 2LL * n_ant;
   const long long P = n_in * (n_in + 1) / 2;
   const long long A = (long long)n_ant * (n_ant + 1) / 2;
@@ -42,6 +43,13 @@ __global__ void dump_dual_kernel(int64_t *__restrict__ acc, int64_t *__restrict_
     // element offsets (in pairs) of XX, XY (p > q only), YX, YY
     const long long e_xx = base + r0 + 2 * q, e_xy = base + r0 + 2 * q + 1;
     const long long e_yx = base + r1 + 2 * q, e_yy = base + r1 + 2 * q + 1;
+#ifdef CORR_DEBUG
+    // every element this thread touches lies in channel c's part of the buffer
+    if (p >= n_ant || q > p || e_xx < base || e_yy >= base + P) {
+      atomicOr(status, kStatusBounds);
+      continue;
+    }
+#endif
     longlong2 *a2 = reinterpret_cast<longlong2 *>(acc);
     const longlong2 zero = make_longlong2(0, 0);
     const longlong2 xx = a2[e_xx], yx = a2[e_yx], yy = a2[e_yy];
@@ -84,6 +92,18 @@ __global__ void dump_single_kernel(int64_t *__restrict__ acc, int64_t *__restric
   }
 }
 
+// Debug builds: one block compares both guard bands with kGuardByte.
+__global__ void guard_check_kernel(const unsigned char *__restrict__ before,
+                                   const unsigned char *__restrict__ after, size_t bytes,
+                                   int *status) {
+  const uint32_t want = 0x01010101u * kGuardByte;
+  bool bad = false;
+  for (size_t w = threadIdx.x; w < bytes / 4; w += blockDim.x)
+    bad |= reinterpret_cast<const uint32_t *>(before)[w] != want ||
+           reinterpret_cast<const uint32_t *>(after)[w] != want;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStatusBounds);
+}
+
 // dst[row][0..pitch) = src[row][0..T) followed by zeros
 __global__ void pitch_kernel(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
                              long long rows, int T, int pitch) {
@@ -97,13 +117,19 @@ __global__ void pitch_kernel(const uint8_t *__restrict__ src, uint8_t *__restric
 }  // namespace
 
 cudaError_t launch_dump(int64_t *acc, int64_t *vis, int64_t *stokes, int n_ant, int n_pol,
-                        int n_chan, cudaStream_t stream, int grid) {
+                        int n_chan, cudaStream_t stream, int grid, int *status) {
   if (n_pol == 2) {
-    dump_dual_kernel<<<grid, 256, 0, stream>>>(acc, vis, stokes, n_ant, n_chan);
+    dump_dual_kernel<<<grid, 256, 0, stream>>>(acc, vis, stokes, n_ant, n_chan, status);
   } else {
     const long long n_in = n_ant;
     dump_single_kernel<<<grid, 256, 0, stream>>>(acc, vis, n_in * (n_in + 1) / 2 * n_chan);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_guard_check(const unsigned char *before, const unsigned char *after,
+                               size_t bytes, int *status, cudaStream_t stream) {
+  guard_check_kernel<<<1, 256, 0, stream>>>(before, after, bytes, status);
   return cudaGetLastError();
 }
 

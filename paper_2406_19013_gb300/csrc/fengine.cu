@@ -17,21 +17,27 @@
 // One CTA (256 threads) takes one input and a tile of kSpecTile consecutive
 // spectra:
 //   - the input's samples stream through a ring of 2048-byte segments in
-//     shared memory (each sample is read from HBM once per tile, plus three
-//     segments of overlap at the tile start);
+//     shared memory, copied in with cp.async one batch ahead (each sample is
+//     read from HBM once per tile, plus three segments of overlap at the
+//     tile start);
 //   - spectra go through in batches of kBatch, so that every barrier of the
 //     FFT is shared by kBatch independent butterflies per thread;
-//   - thread t filters samples 4 t .. 4 t + 3 and 1024 + 4 t .. + 3 (filter
-//     coefficients read from L1 per tap, int8 samples turned into fp32 with a
-//     byte permute and an exact subtraction), and pairs them as
-//     z[m] = v[2m] + i v[2m+1];
+//   - thread t owns samples 4 t .. 4 t + 3 and 1024 + 4 t .. + 3 of every
+//     segment and filters a batch's spectra together: each of the batch's
+//     kBatch + 3 segments is turned into fp32 once (a byte permute and an
+//     exact subtraction) and feeds every spectrum of the batch whose taps
+//     cover it, with the thread's 32 filter coefficients loaded once per
+//     batch; it pairs the results as z[m] = v[2m] + i v[2m+1];
 //   - a 1024-point complex FFT runs in three in-place passes over shared
 //     memory, 1024 = 16 x 4 x 16 (each thread does a 16-point FFT in registers
-//     in the first and last pass, four 4-point FFTs in the middle one), then
-//     the standard split gives the 2048-point real FFT's channels 0..1023;
-//   - EQ and requantisation produce one byte per channel into a staging tile
-//     [kSpecTile spectra][1024 channels], written out as 32-byte runs of
-//     out[c][input][k0 ..].
+//     in the first and last pass, four 4-point FFTs in the middle one);
+//   - the standard split of the real FFT, folded with the EQ gain into two
+//     complex constants per channel, gives g X[c] = A_c Z[c] + B_c conj Z[N-c]
+//     (A_c = g (1 - i W_2048^c) / 2, B_c = g (1 + i W_2048^c) / 2), then
+//     requantisation; each thread packs one channel's codes of the batch's 4
+//     spectra into a word of a staging tile [1024 channels][kSpecTile spectra];
+//   - each channel's row of the staging tile is written out as one 32-byte run
+//     of out[c][input][k0 ..].
 // Floating point is fp32 (the host computes the filter and twiddles in
 // double precision); the codes can differ from an exact computation only for
 // values within the fp32 rounding error of a quantisation boundary.
@@ -44,6 +50,7 @@
 #include <vector>
 
 #include "corr.h"
+#include "trace.h"
 
 namespace {
 
@@ -52,6 +59,7 @@ constexpr int kTaps = 4;
 constexpr int kHalf = kP / 2;     // channels; also the complex FFT size
 constexpr int kThreads = 256;
 constexpr int kSpecTile = 32;     // spectra per CTA tile
+constexpr int kCtasPerSm = 2;     // resident CTAs per SM the kernel is built for
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -100,16 +108,23 @@ __device__ __forceinline__ void dft16(float2 (&a)[16]) {
     }
 }
 
+// Round half away from zero, then clip to [-7, 7] (the clip bounds are
+// integers, so clipping first gives the same code).  The half is added with
+// rounding toward zero, so the sum never reaches the next integer unless the
+// exact sum does, and the truncation then gives the rounded value exactly.
 __device__ __forceinline__ int quant(float a) {
-  const float r = roundf(a);  // half away from zero
-  return (int)fminf(fmaxf(r, -7.0f), 7.0f);
+  const float y = fminf(fmaxf(a, -7.0f), 7.0f);
+  return __float2int_rz(__fadd_rz(y, copysignf(0.5f, y)));
 }
 
 // Shared memory of one CTA (dynamic): the sample ring, the FFT buffers of a
 // batch of spectra and, when quantising, the staging tile.
 constexpr int kBatch = 4;                         // spectra per inner iteration
-constexpr int kRing = 8;                          // ring slots (>= kTaps - 1 + kBatch)
-constexpr int kRingBytes = kRing * kP;            // 16 KB
+// Ring of sample segments: a batch reads kBatch + 3 of them while the next
+// batch's kBatch newest ones are being copied in (cp.async), so the copies
+// of HBM data overlap a whole batch of compute.
+constexpr int kRing = 16;                         // ring slots (>= kTaps - 1 + 2 kBatch)
+constexpr int kRingBytes = kRing * kP;            // 32 KB
 // FFT buffers: element e of a spectrum sits at e + e / 64 (one pad element
 // per 64).  That keeps the passes' runs of consecutive elements and their
 // stride-64 gathers at the two shared-memory wavefronts a warp's float2
@@ -117,86 +132,124 @@ constexpr int kRingBytes = kRing * kP;            // 16 KB
 // plus a constant offset.
 constexpr int kBufElems = kHalf + kHalf / 64;
 constexpr int kBufBytes = kBatch * kBufElems * 8;
-constexpr int kStageBytes = kHalf * kSpecTile;    // 32 KB, [spectrum][channel]
+
+// Staging tile: [channel][kSpecTile codes], rows kStagePitch bytes apart.
+// 36 = 9 words, so the 4-byte stores and loads of 32 consecutive channels
+// fall in 32 distinct banks.
+constexpr int kStagePitch = kSpecTile + 4;
+constexpr int kStageBytes = kHalf * kStagePitch;  // 36 KB
 
 __device__ __forceinline__ int bpos(int e) { return e + (e >> 6); }
+
+// 8-byte asynchronous copy global -> shared; src_bytes 0 writes zeros.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, int src_bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 static_assert(kSpecTile % kBatch == 0, "tile of whole batches");
-static_assert(kRing >= kTaps - 1 + kBatch && (kRing & (kRing - 1)) == 0, "ring size");
+static_assert(kRing >= kTaps - 1 + 2 * kBatch && (kRing & (kRing - 1)) == 0, "ring size");
 
 // kQuant: 1 -> packed codes via the staging tile; 0 -> float2 g X straight to
 // global (X-engine order, for tolerance checks).
 template <int kQuant>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
     fengine_kernel(const int8_t *__restrict__ adc, const float *__restrict__ proto,
-                   const float2 *__restrict__ tw_fft, const float2 *__restrict__ tw_split,
-                   const float *__restrict__ eq, uint8_t *__restrict__ out_codes,
-                   float2 *__restrict__ out_spec, int n_in, int n_spec) {
+                   const float2 *__restrict__ tw_fft, const float2 *__restrict__ split_a,
+                   const float2 *__restrict__ split_b, const float *__restrict__ eq,
+                   uint8_t *__restrict__ out_codes, float2 *__restrict__ out_spec, int n_in,
+                   int n_spec) {
   extern __shared__ __align__(16) uint8_t fe_smem[];
   int8_t *ring = reinterpret_cast<int8_t *>(fe_smem);                      // [kRing][kP]
   float2 *buf = reinterpret_cast<float2 *>(fe_smem + kRingBytes);  // [kBatch][kBufElems]
-  uint8_t *stage = fe_smem + kRingBytes + kBufBytes;               // [kSpecTile][kHalf]
+  uint8_t *stage = fe_smem + kRingBytes + kBufBytes;               // [kHalf][kStagePitch]
   const int tid = threadIdx.x;
   // W64^j = W1024^(16 j), the first pass's twiddles, kept in shared memory
   __shared__ float2 tw64[64];
   if (tid < 64) tw64[tid] = __ldg(tw_fft + 16 * tid);
   __syncthreads();
   const int n_tiles = (n_spec + kSpecTile - 1) / kSpecTile;
-  const long long stream_len = (long long)(n_spec + kTaps - 1) * kP;
+  const int n_seg = n_spec + kTaps - 1;  // segments in one input's stream
+  const long long stream_len = (long long)n_seg * kP;
+
+  // starts the copy of this thread's 8 bytes of segment seg into its ring
+  // slot; segments past the stream's end read as zero (they feed only
+  // spectra past n_spec, which are computed and dropped)
+  auto fetch_seg = [&](const int8_t *x, int seg) {
+    const bool in = seg < n_seg;
+    cp_async8(&ring[(seg & (kRing - 1)) * kP + 8 * tid],
+              x + (in ? (long long)seg * kP + 8 * tid : 0), in ? 8 : 0);
+  };
 
   for (long long w = blockIdx.x; w < (long long)n_in * n_tiles; w += gridDim.x) {
     const int in = (int)(w / n_tiles), tile = (int)(w % n_tiles);
     const int k0 = tile * kSpecTile;
     const int ns = min(kSpecTile, n_spec - k0);
     const int8_t *x = adc + (long long)in * stream_len;
-    // prime the ring with segments k0 .. k0 + 2
-    for (int j = 0; j < kTaps - 1; ++j)
-      *reinterpret_cast<uint2 *>(&ring[((k0 + j) & (kRing - 1)) * kP + 8 * tid]) =
-          __ldg(reinterpret_cast<const uint2 *>(x + (long long)(k0 + j) * kP + 8 * tid));
-    for (int s0 = 0; s0 < ns; s0 += kBatch) {
-      const int nb = min(kBatch, ns - s0);  // spectra in this batch
-      // newest segments k0 + s0 + 3 .. + nb + 2
-      for (int u = 0; u < nb; ++u) {
-        const int seg = k0 + s0 + u + kTaps - 1;
-        *reinterpret_cast<uint2 *>(&ring[(seg & (kRing - 1)) * kP + 8 * tid]) =
-            __ldg(reinterpret_cast<const uint2 *>(x + (long long)seg * kP + 8 * tid));
-      }
-      __syncthreads();
-      // ---- polyphase FIR of each spectrum of the batch.  The filter
-      // coefficients of this thread's 8 samples (4 tid .. + 3 and 1024 + 4 tid
-      // .. + 3 of the 2048) are read from L1 per tap, so that they do not stay
-      // live through the FFT passes.
-#pragma unroll 1
-      for (int u = 0; u < nb; ++u) {
-        const int k = k0 + s0 + u;
-        float v[8];
+    // the first batch's segments k0 .. k0 + kBatch + 2
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = 0.0f;
+    for (int j = 0; j < kBatch + kTaps - 1; ++j) fetch_seg(x, k0 + j);
+    cp_async_commit();
+    for (int s0 = 0; s0 < ns; s0 += kBatch) {
+      const int nb = min(kBatch, ns - s0);  // spectra of this batch that are kept
+      // the next batch's newest segments, while this batch computes
+      if (s0 + kBatch < ns) {
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) fetch_seg(x, k0 + s0 + kBatch + kTaps - 1 + u);
+      }
+      cp_async_commit();
+      cp_async_wait<1>();  // this batch's segments have landed (this thread's part)
+      __syncthreads();     // ... and every thread's
+      // ---- polyphase FIR of the batch's kBatch spectra.  Thread t owns
+      // samples 4 t .. 4 t + 3 and 1024 + 4 t .. + 3 of every segment; segment
+      // k0 + s0 + sg is tap j = sg - u of spectrum k0 + s0 + u, and the taps
+      // of a spectrum are summed in the order j = 0, 1, 2, 3.
+      {
+        float h[kTaps][8];
 #pragma unroll
         for (int j = 0; j < kTaps; ++j) {
-          const int8_t *seg = &ring[((k + j) & (kRing - 1)) * kP];
           const float4 h0 = __ldg(reinterpret_cast<const float4 *>(proto + j * kP + 4 * tid));
           const float4 h1 = __ldg(reinterpret_cast<const float4 *>(proto + j * kP + kHalf + 4 * tid));
-          const float hc[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+          h[j][0] = h0.x; h[j][1] = h0.y; h[j][2] = h0.z; h[j][3] = h0.w;
+          h[j][4] = h1.x; h[j][5] = h1.y; h[j][6] = h1.z; h[j][7] = h1.w;
+        }
+        float v[kBatch][8];
+#pragma unroll
+        for (int sg = 0; sg < kBatch + kTaps - 1; ++sg) {
+          const int8_t *seg = &ring[((k0 + s0 + sg) & (kRing - 1)) * kP];
           // int8 -> fp32 without a conversion instruction: with the sign bit
           // flipped, byte b + 128 placed under the exponent of 2^23 is the
           // float 2^23 + b + 128, and subtracting 2^23 + 128 is exact
           const uint32_t wd[2] = {*reinterpret_cast<const uint32_t *>(seg + 4 * tid) ^ 0x80808080u,
                                   *reinterpret_cast<const uint32_t *>(seg + kHalf + 4 * tid) ^
                                       0x80808080u};
+          float xs[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const uint32_t f = __byte_perm(wd[e >> 2], 0x4B000000u, 0x7650 + (e & 3));
-            const float xs = __uint_as_float(f) - 8388736.0f;
-            v[e] = fmaf(hc[e], xs, v[e]);
+          for (int e = 0; e < 8; ++e)
+            xs[e] = __uint_as_float(__byte_perm(wd[e >> 2], 0x4B000000u, 0x7650 + (e & 3))) -
+                    8388736.0f;
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const int j = sg - u;
+            if (j < 0 || j >= kTaps) continue;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[u][e] = j == 0 ? h[0][e] * xs[e] : fmaf(h[j][e], xs[e], v[u][e]);
           }
         }
         // z[2 tid], z[2 tid + 1] and z[512 + 2 tid], z[513 + 2 tid]
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float2 *d = &buf[u * kBufElems + bpos(512 * h + 2 * tid)];
-          d[0] = make_float2(v[4 * h], v[4 * h + 1]);
-          d[1] = make_float2(v[4 * h + 2], v[4 * h + 3]);
-        }
+        for (int u = 0; u < kBatch; ++u)
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            float2 *d = &buf[u * kBufElems + bpos(512 * hh + 2 * tid)];
+            d[0] = make_float2(v[u][4 * hh], v[u][4 * hh + 1]);
+            d[1] = make_float2(v[u][4 * hh + 2], v[u][4 * hh + 3]);
+          }
       }
       __syncthreads();
       // ---- 1024-point FFTs, 1024 = 16 x 4 x 16 (n = 64 m1 + 16 m2 + n2,
@@ -261,52 +314,48 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
       }
       __syncthreads();
-      // ---- real-FFT split, EQ, requantisation: channels c = tid + 256 e
+      // ---- real-FFT split with the EQ gain, requantisation: channels
+      // c = tid + 256 e.  With Z[c] = p + i q and Z[N - c] = r + i s,
+      //   g X[c] = A Z[c] + B conj Z[N - c]
+      //          = (A.x p - A.y q + B.x r + B.y s) + i (A.x q + A.y p + B.y r - B.x s).
 #pragma unroll 1
       for (int e = 0; e < 4; ++e) {
         const int c = tid + kThreads * e;
-        const float2 tw = __ldg(tw_split + c);
         const float g = __ldg(eq + (long long)in * kHalf + c);  // EQ gain
+        const float2 sa = __ldg(split_a + c), sb = __ldg(split_b + c);
+        const float2 A = make_float2(g * sa.x, g * sa.y), B = make_float2(g * sb.x, g * sb.y);
+        const int cr = (kHalf - c) & (kHalf - 1);
+        uint32_t word = 0;
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
-          if (u >= nb) break;
           const float2 zc = buf[u * kBufElems + bpos(c)];
-          const float2 zr = buf[u * kBufElems + bpos((kHalf - c) & (kHalf - 1))];
-          // even part (Z[c] + conj Z[N-c]) / 2, odd part (Z[c] - conj Z[N-c]) / (2i)
-          const float2 ev = make_float2(0.5f * (zc.x + zr.x), 0.5f * (zc.y - zr.y));
-          const float2 od = make_float2(0.5f * (zc.y + zr.y), -0.5f * (zc.x - zr.x));
-          const float2 t = cmul(tw, od);
-          const float2 gX = make_float2(g * (ev.x + t.x), g * (ev.y + t.y));
+          const float2 zr = buf[u * kBufElems + bpos(cr)];
+          const float gx = fmaf(A.x, zc.x, fmaf(-A.y, zc.y, fmaf(B.x, zr.x, B.y * zr.y)));
+          const float gy = fmaf(A.x, zc.y, fmaf(A.y, zc.x, fmaf(B.y, zr.x, -B.x * zr.y)));
           if (kQuant) {
-            const int qr = quant(gX.x), qi = quant(gX.y);
-            stage[(s0 + u) * kHalf + c] = (uint8_t)(((qr & 15) << 4) | (qi & 15));
-          } else {
-            out_spec[((long long)c * n_in + in) * n_spec + k0 + s0 + u] = gX;
+            const int qr = quant(gx), qi = quant(gy);
+            word |= (uint32_t)(((qr & 15) << 4) | (qi & 15)) << (8 * u);
+          } else if (u < nb) {
+            out_spec[((long long)c * n_in + in) * n_spec + k0 + s0 + u] = make_float2(gx, gy);
           }
         }
+        if (kQuant) *reinterpret_cast<uint32_t *>(&stage[c * kStagePitch + s0]) = word;
       }
       __syncthreads();  // buf and the ring slots are reused by the next batch
     }
     if (kQuant) {
       // ---- staging tile -> out[c][in][k0 .. k0 + ns): thread per channel,
-      // gathering its column of the tile (consecutive channels read
-      // consecutive bytes, so the gathers are conflict-free)
+      // its row of the tile as eight words (conflict-free: rows 9 words apart)
       const bool vec = ns == kSpecTile && (n_spec & 15) == 0;
       static_assert(kSpecTile == 32, "two 16-byte stores per channel");
       for (int c = tid; c < kHalf; c += kThreads) {
-        uint32_t wv[8];
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          wv[b] = 0;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) wv[b] |= (uint32_t)stage[(4 * b + k) * kHalf + c] << (8 * k);
-        }
+        const uint32_t *row = reinterpret_cast<const uint32_t *>(&stage[c * kStagePitch]);
         uint8_t *dst = out_codes + ((long long)c * n_in + in) * n_spec + k0;
         if (vec) {
-          reinterpret_cast<uint4 *>(dst)[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-          reinterpret_cast<uint4 *>(dst)[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+          reinterpret_cast<uint4 *>(dst)[0] = make_uint4(row[0], row[1], row[2], row[3]);
+          reinterpret_cast<uint4 *>(dst)[1] = make_uint4(row[4], row[5], row[6], row[7]);
         } else {
-          for (int b = 0; b < ns; ++b) dst[b] = stage[b * kHalf + c];
+          for (int b = 0; b < ns; ++b) dst[b] = stage[c * kStagePitch + b];
         }
       }
       __syncthreads();
@@ -314,14 +363,14 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
-constexpr int smem_bytes(int quant) { return kRingBytes + kBufBytes + (quant ? kStageBytes : 0); }
+constexpr int smem_bytes() { return kRingBytes + kBufBytes + kStageBytes; }
 
 }  // namespace
 
 struct corr_fengine {
   int n_in, n_spec, n_sm;
   float *d_proto;
-  float2 *d_tw_fft, *d_tw_split;
+  float2 *d_tw_fft, *d_split_a, *d_split_b;
   float *d_eq;
 };
 
@@ -337,7 +386,8 @@ void free_fengine(corr_fengine *f) {
   if (!f) return;
   cudaFree(f->d_proto);
   cudaFree(f->d_tw_fft);
-  cudaFree(f->d_tw_split);
+  cudaFree(f->d_split_a);
+  cudaFree(f->d_split_b);
   cudaFree(f->d_eq);
   delete f;
 }
@@ -373,27 +423,35 @@ int corr_fengine_create(int n_in, int n_spectra, corr_fengine **out) {
     const double sinc = xx == 0.0 ? 1.0 : std::sin(pi * xx) / (pi * xx);
     proto[m] = (float)(w * sinc);
   }
-  std::vector<float2> tw_fft(kHalf), tw_split(kHalf);
+  // FFT twiddles W_1024^k, and the real-FFT split's constants per channel:
+  // with W = W_2048^c = cos t - i sin t (t = 2 pi c / 2048),
+  // (1 - i W) / 2 = ((1 - sin t) / 2, -cos t / 2) and (1 + i W) / 2 = ((1 + sin t) / 2, cos t / 2)
+  std::vector<float2> tw_fft(kHalf), split_a(kHalf), split_b(kHalf);
   for (int k = 0; k < kHalf; ++k) {
     tw_fft[k] = make_float2((float)std::cos(2.0 * pi * k / kHalf), (float)-std::sin(2.0 * pi * k / kHalf));
-    tw_split[k] = make_float2((float)std::cos(2.0 * pi * k / kP), (float)-std::sin(2.0 * pi * k / kP));
+    const double t = 2.0 * pi * k / kP, ct = std::cos(t), st = std::sin(t);
+    split_a[k] = make_float2((float)(0.5 * (1.0 - st)), (float)(-0.5 * ct));
+    split_b[k] = make_float2((float)(0.5 * (1.0 + st)), (float)(0.5 * ct));
   }
   int rc;
   if ((rc = cuda_err(cudaFuncSetAttribute(fengine_kernel<1>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          smem_bytes(1)))) != CORR_OK ||
+                                          smem_bytes()))) != CORR_OK ||
       (rc = cuda_err(cudaFuncSetAttribute(fengine_kernel<0>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          smem_bytes(0)))) != CORR_OK ||
+                                          smem_bytes()))) != CORR_OK ||
       (rc = cuda_err(cudaMalloc(&f->d_proto, L * sizeof(float)))) != CORR_OK ||
       (rc = cuda_err(cudaMalloc(&f->d_tw_fft, kHalf * sizeof(float2)))) != CORR_OK ||
-      (rc = cuda_err(cudaMalloc(&f->d_tw_split, kHalf * sizeof(float2)))) != CORR_OK ||
+      (rc = cuda_err(cudaMalloc(&f->d_split_a, kHalf * sizeof(float2)))) != CORR_OK ||
+      (rc = cuda_err(cudaMalloc(&f->d_split_b, kHalf * sizeof(float2)))) != CORR_OK ||
       (rc = cuda_err(cudaMalloc(&f->d_eq, eq.size() * sizeof(float)))) != CORR_OK ||
       (rc = cuda_err(cudaMemcpy(f->d_proto, proto.data(), L * sizeof(float),
                                 cudaMemcpyHostToDevice))) != CORR_OK ||
       (rc = cuda_err(cudaMemcpy(f->d_tw_fft, tw_fft.data(), kHalf * sizeof(float2),
                                 cudaMemcpyHostToDevice))) != CORR_OK ||
-      (rc = cuda_err(cudaMemcpy(f->d_tw_split, tw_split.data(), kHalf * sizeof(float2),
+      (rc = cuda_err(cudaMemcpy(f->d_split_a, split_a.data(), kHalf * sizeof(float2),
+                                cudaMemcpyHostToDevice))) != CORR_OK ||
+      (rc = cuda_err(cudaMemcpy(f->d_split_b, split_b.data(), kHalf * sizeof(float2),
                                 cudaMemcpyHostToDevice))) != CORR_OK ||
       (rc = cuda_err(cudaMemcpy(f->d_eq, eq.data(), eq.size() * sizeof(float),
                                 cudaMemcpyHostToDevice))) != CORR_OK) {
@@ -411,20 +469,22 @@ int corr_fengine_set_eq(corr_fengine *f, const float *h_eq) {
 }
 
 int corr_fengine_run(corr_fengine *f, const int8_t *d_adc, uint8_t *d_out, void *stream) {
+  CORR_TRACE("corr_fengine_run");
   if (!f || !d_adc || !d_out || !aligned(d_adc, 8) || !aligned(d_out, 16)) return CORR_EINVAL;
   const long long work = (long long)f->n_in * ((f->n_spec + kSpecTile - 1) / kSpecTile);
-  const int grid = (int)std::min<long long>(work, (long long)f->n_sm * 8);
-  fengine_kernel<1><<<grid, kThreads, smem_bytes(1), static_cast<cudaStream_t>(stream)>>>(
-      d_adc, f->d_proto, f->d_tw_fft, f->d_tw_split, f->d_eq, d_out, nullptr, f->n_in, f->n_spec);
+  const int grid = (int)std::min<long long>(work, (long long)f->n_sm * kCtasPerSm * 4);
+  fengine_kernel<1><<<grid, kThreads, smem_bytes(), static_cast<cudaStream_t>(stream)>>>(
+      d_adc, f->d_proto, f->d_tw_fft, f->d_split_a, f->d_split_b, f->d_eq, d_out, nullptr, f->n_in, f->n_spec);
   return cuda_err(cudaGetLastError());
 }
 
 int corr_fengine_spectra(corr_fengine *f, const int8_t *d_adc, float *d_spec, void *stream) {
+  CORR_TRACE("corr_fengine_spectra");
   if (!f || !d_adc || !d_spec || !aligned(d_adc, 8) || !aligned(d_spec, 8)) return CORR_EINVAL;
   const long long work = (long long)f->n_in * ((f->n_spec + kSpecTile - 1) / kSpecTile);
-  const int grid = (int)std::min<long long>(work, (long long)f->n_sm * 8);
-  fengine_kernel<0><<<grid, kThreads, smem_bytes(0), static_cast<cudaStream_t>(stream)>>>(
-      d_adc, f->d_proto, f->d_tw_fft, f->d_tw_split, f->d_eq, nullptr,
+  const int grid = (int)std::min<long long>(work, (long long)f->n_sm * kCtasPerSm * 4);
+  fengine_kernel<0><<<grid, kThreads, smem_bytes(), static_cast<cudaStream_t>(stream)>>>(
+      d_adc, f->d_proto, f->d_tw_fft, f->d_split_a, f->d_split_b, f->d_eq, nullptr,
       reinterpret_cast<float2 *>(d_spec), f->n_in, f->n_spec);
   return cuda_err(cudaGetLastError());
 }

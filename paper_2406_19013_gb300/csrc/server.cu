@@ -49,6 +49,7 @@
 #include <vector>
 
 #include "corr.h"
+#include "trace.h"
 
 namespace {
 
@@ -177,6 +178,21 @@ struct corr_server {
   std::deque<corr_result> results;
   bool stop = false, flush_req = false;
   int error = CORR_OK;
+  // events of finished blocks, reused by later blocks (worker only), so that
+  // the steady state creates no events
+  std::vector<cudaEvent_t> ev_pool;
+  bool take_event(cudaEvent_t *e) {
+    if (!ev_pool.empty()) {
+      *e = ev_pool.back();
+      ev_pool.pop_back();
+      return true;
+    }
+    return cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+  }
+  void give_event(cudaEvent_t &e) {
+    if (e) ev_pool.push_back(e);
+    e = nullptr;
+  }
   // statistics
   long long n_submitted = 0, n_integrated = 0, n_dup = 0, n_late = 0, n_incomplete = 0,
             n_integrations = 0;
@@ -251,7 +267,8 @@ bool corr_server::admit() {
     if (off == SIZE_MAX) break;  // full: later blocks wait behind this one
     b->off = off;
     if (!dry) {
-      if (cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming) != cudaSuccess ||
+      CORR_TRACE("server_copy_block");
+      if (!take_event(&b->copied) ||
           cudaMemcpyAsync(d_arena + off, b->h, a.block_bytes, cudaMemcpyHostToDevice, s_copy) !=
               cudaSuccess ||
           cudaEventRecord(b->copied, s_copy) != cudaSuccess) {
@@ -311,10 +328,10 @@ bool corr_server::progress(int ai) {
     Blk &b = bk.second;
     if (b.state != kCopied) continue;
     if (!dry) {
+      CORR_TRACE("server_push_block");
       if (cudaStreamWaitEvent(a.s_compute, b.copied, 0) != cudaSuccess ||
           corr_push_block(a.ctx, d_arena + b.off, a.s_compute) != CORR_OK ||
-          cudaEventCreateWithFlags(&b.pushed, cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventRecord(b.pushed, a.s_compute) != cudaSuccess) {
+          !take_event(&b.pushed) || cudaEventRecord(b.pushed, a.s_compute) != cudaSuccess) {
         error = CORR_ECUDA;
         return false;
       }
@@ -352,6 +369,7 @@ bool corr_server::progress(int ai) {
   }
   res.vis = dry ? nullptr : a.h_vis;
   if (!dry) {
+    CORR_TRACE("server_dump");
     if (corr_dump(a.ctx, a.d_vis, nullptr, a.s_compute) != CORR_OK ||
         cudaEventRecord(a.dumped, a.s_compute) != cudaSuccess ||
         cudaStreamWaitEvent(s_out, a.dumped, 0) != cudaSuccess ||
@@ -406,8 +424,8 @@ bool corr_server::step() {
       if (done) {
         if (!dry)
           for (auto &bk : it->second.blocks) {
-            if (bk.second.copied) cudaEventDestroy(bk.second.copied);
-            if (bk.second.pushed) cudaEventDestroy(bk.second.pushed);
+            give_event(bk.second.copied);
+            give_event(bk.second.pushed);
           }
         it = a.integ.erase(it);
       } else {
@@ -472,6 +490,7 @@ void free_server(corr_server *s) {
           if (bk.second.pushed) cudaEventDestroy(bk.second.pushed);
         }
     }
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     cudaFree(s->d_arena);
     if (s->s_copy) cudaStreamDestroy(s->s_copy);
     if (s->s_out) cudaStreamDestroy(s->s_out);
@@ -486,6 +505,7 @@ extern "C" {
 
 int corr_server_create(int n_arrays, const corr_array_desc *desc, size_t arena_bytes, int window,
                        int flags, corr_server **out) {
+  CORR_TRACE("corr_server_create");
   if (!out) return CORR_EINVAL;
   *out = nullptr;
   if (n_arrays <= 0 || !desc || window < 1 || (flags & ~CORR_SERVER_DRY)) return CORR_EINVAL;

@@ -99,6 +99,29 @@ struct XItem {
   int prob, tpl, chan, pk0, npk;
 };
 
+// Bits of the device status word.
+constexpr int kStatusTimeout = 1;  // a bounded wait ran out
+constexpr int kStatusBounds = 2;   // debug builds: an address check or a guard band failed
+
+// Atomic add into an int64 integration buffer of `elems` elements.  Debug
+// builds (CORR_DEBUG) check the address first: one outside the buffer sets
+// kStatusBounds and the add is skipped.  Release builds add unchecked.
+__device__ __forceinline__ void acc_add(int64_t *base, long long elems, int *status, int64_t *ptr,
+                                        long long v) {
+#ifdef CORR_DEBUG
+  const long long off = ptr - base;
+  if (off < 0 || off >= elems) {
+    atomicOr(status, kStatusBounds);
+    return;
+  }
+#else
+  (void)base;
+  (void)elems;
+  (void)status;
+#endif
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(ptr), "l"((unsigned long long)v) : "memory");
+}
+
 struct XParams {
   const XProb *probs;
   // Explicit items: CTA b runs items [cta_first[b], cta_first[b + 1]).
@@ -108,7 +131,7 @@ struct XParams {
   const XItem *items;
   const int *cta_first;
   int implicit_n_tpl, implicit_n_chan, implicit_npk;
-  int *status;           // device status word (bit 0: a wait timed out)
+  int *status;           // device status word (kStatusTimeout | kStatusBounds)
   unsigned long long timeout_ns;
   int z_stages, pk_stages;
   uint32_t z_stage_bytes, pk_stage_bytes;
@@ -192,8 +215,16 @@ cudaError_t cmac_set_smem(int smem_bytes);
 cudaError_t launch_cmac_tm(const XMaps &maps, const XParams &p, int grid, int smem_bytes,
                            cudaStream_t stream);
 cudaError_t cmac_tm_set_smem(int smem_bytes);
+// status: the owner's device status word (debug builds set kStatusBounds on a
+// failed address check; release builds ignore it).
 cudaError_t launch_dump(int64_t *acc, int64_t *vis, int64_t *stokes, int n_ant, int n_pol,
-                        int n_chan, cudaStream_t stream, int grid);
+                        int n_chan, cudaStream_t stream, int grid, int *status);
+// Debug builds: checks that the guard bands of `bytes` before and after a
+// buffer still hold kGuardByte, else sets kStatusBounds.
+constexpr unsigned char kGuardByte = 0xA5;
+constexpr size_t kGuardBytes = 4096;
+cudaError_t launch_guard_check(const unsigned char *before, const unsigned char *after,
+                               size_t bytes, int *status, cudaStream_t stream);
 cudaError_t launch_pitch(const uint8_t *src, uint8_t *dst, long long rows, int T, int pitch,
                          cudaStream_t stream, int grid);
 cudaError_t launch_corner_turn(const uint8_t *src, uint8_t *dst, int n_in, int n_chan,

@@ -1,5 +1,5 @@
 // xe_unpack.cuh -- on-chip unpack of 4+4-bit samples into E5M2 operand rows,
-// shared-memory access helpers and the int64 fold, shared by the CMAC kernels.
+// shared-memory access helpers, shared by the CMAC kernels.
 #pragma once
 #include <cstdint>
 
@@ -81,11 +81,5 @@ __device__ __forceinline__ void transpose4(uint32_t i0, uint32_t i1, uint32_t i2
   o2 = __byte_perm(hi01, hi23, 0x5410);
   o3 = __byte_perm(hi01, hi23, 0x7632);
 }
-
-// Fire-and-forget 64-bit add in L2 (no return value, no round trip).
-__device__ __forceinline__ void red_add_s64(int64_t *addr, long long v) {
-  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(addr), "l"((unsigned long long)v) : "memory");
-}
-
 
 }  // namespace xe

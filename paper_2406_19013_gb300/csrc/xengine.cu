@@ -419,6 +419,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int i = sgm.row_in0 + 8 * g + l_in;
         const bool row_ok = i < pb.n_in;
         int64_t *arow = pb.acc + ((long long)c * pb.n_pairs + (long long)i * (i + 1) / 2) * 2;
+        const long long acc_elems = (long long)pb.n_chan * pb.n_pairs * 2;
         for (int cb = 0; cb < sgm.n; cb += 16) {
           uint32_t v[16];
           __syncwarp();
@@ -441,8 +442,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int e = 0; e < 8; ++e) {
               const int jj = j0 + ((e - rot) & 7);
               if (row_ok && jj <= i) {
-                red_add_s64(arow + 2 * (long long)jj, re[e]);
-                red_add_s64(arow + 2 * (long long)jj + 1, im[e]);
+                acc_add(pb.acc, acc_elems, p.status, arow + 2 * (long long)jj, re[e]);
+                acc_add(pb.acc, acc_elems, p.status, arow + 2 * (long long)jj + 1, im[e]);
               }
             }
           } else {
@@ -451,8 +452,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int e = 0; e < 8; ++e)
               if (e < nvalid) {
-                red_add_s64(ptr + 2 * e, re[e]);
-                red_add_s64(ptr + 2 * e + 1, im[e]);
+                acc_add(pb.acc, acc_elems, p.status, ptr + 2 * e, re[e]);
+                acc_add(pb.acc, acc_elems, p.status, ptr + 2 * e + 1, im[e]);
               }
           }
         }

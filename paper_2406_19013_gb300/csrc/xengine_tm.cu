@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(kTmThreads, 1)
   }
   const uint64_t to = p.timeout_ns;
   const XProb pb = p.probs[0];
+  const long long acc_elems = (long long)pb.n_chan * pb.n_pairs * 2;
   const int n_st = kTileInputs * G.n_rt;  // staged inputs
 
   if (warp == kWarpTma) {
@@ -372,8 +373,8 @@ __global__ void __launch_bounds__(kTmThreads, 1)
 #pragma unroll
           for (int e = 0; e < 8; ++e)
             if (e < nvalid) {
-              red_add_s64(ptr + 2 * e, re[e]);
-              red_add_s64(ptr + 2 * e + 1, im[e]);
+              acc_add(pb.acc, acc_elems, p.status, ptr + 2 * e, re[e]);
+              acc_add(pb.acc, acc_elems, p.status, ptr + 2 * e + 1, im[e]);
             }
         }
       }
@@ -399,7 +400,9 @@ __global__ void __launch_bounds__(kTmThreads, 1)
           int64_t *ptr = arow + 2 * (long long)j0;
 #pragma unroll
           for (int e = 0; e < 16; ++e)
-            if (e < nvalid) red_add_s64(ptr + 2 * e, __float2int_rn(__uint_as_float(v[e])));
+            if (e < nvalid)
+              acc_add(pb.acc, acc_elems, p.status, ptr + 2 * e,
+                      __float2int_rn(__uint_as_float(v[e])));
         }
       }
       tc_fence_before();

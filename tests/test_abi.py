@@ -179,3 +179,29 @@ def test_plan_items_rejects(corr):
 
 def test_tuned_cover_is_empty_without_a_gpu(corr):
     assert corr.tuned_cover(192, 8192) == -1
+
+
+def test_stats_snapshot_restore_reject_null(corr):
+    lib = corr.load()
+    st = corr.Stats()
+    n = corr._ll()
+    assert lib.corr_get_stats(None, corr.ctypes.byref(st)) == corr.CORR_EINVAL
+    assert lib.corr_snapshot(None, None, corr.ctypes.byref(n), None) == corr.CORR_EINVAL
+    assert lib.corr_restore(None, None, 0, None) == corr.CORR_EINVAL
+    assert lib.corr_debug_corrupt_guard(None, 0) == corr.CORR_EINVAL
+    assert lib.corr_debug_build() == 0
+    assert corr.strerror(corr.CORR_EBOUNDS).startswith("an address check")
+
+
+def test_debug_variant_builds_and_exports(corr):
+    """The debug build (CORR_DEBUG) compiles and exports the same symbols, and
+    says that it is the debug build."""
+    import ctypes
+    from paper_2406_19013_gb300 import build
+    path = build.build(debug=True)
+    assert path.endswith("libcorr_debug.so")
+    lib = ctypes.CDLL(path)
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    lib.corr_debug_build.restype = ctypes.c_int
+    assert lib.corr_debug_build() == 1
