@@ -166,11 +166,19 @@ int corr_plan(int n_in, uint8_t *cover, int *n_units, long long *issued_cmacs);
  *           64-input row tiles' strips share it, packed into 512 TMEM columns.
  *   STRIPS: N <= 256.  One unit per row tile t, staging inputs [0, 64(t+1)).
  *   PAIRS:  any N.  Pairs of row tiles against 256-column pieces of their
- *           strip; the cover used above 256 inputs.
- * WINDOW and STRIPS fall back to PAIRS above 256 inputs. */
+ *           strip; one CTA per unit.
+ *   QUADS:  N > 256.  Blocks of 256 rows against 256-column pieces of their
+ *           strip, each run by a pair of CTAs on two SMs (a 2-CTA cluster):
+ *           each CTA stages 128 of the rows and half of the piece's columns,
+ *           and the pair's M = 256 tensor-core MMAs share the columns.
+ *           Contexts use it only when CORR_CMAC_KERNEL=pair is set.
+ * WINDOW and STRIPS fall back to PAIRS above 256 inputs, QUADS to PAIRS at
+ * 256 and below.  CORR_CMAC_KERNEL=pair in the environment makes contexts of
+ * more than 256 inputs use QUADS, =smem PAIRS. */
 #define CORR_COVER_WINDOW 0
 #define CORR_COVER_STRIPS 1
 #define CORR_COVER_PAIRS 2
+#define CORR_COVER_QUADS 3
 
 /* As corr_plan, for the given cover.  Errors: CORR_EINVAL (n_in out of
  * range, unknown cover). */

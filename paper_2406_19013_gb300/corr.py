@@ -35,6 +35,7 @@ CORR_MAX_INPUTS = 8192
 CORR_COVER_WINDOW = 0
 CORR_COVER_STRIPS = 1
 CORR_COVER_PAIRS = 2
+CORR_COVER_QUADS = 3
 CORR_BATCH_AUTOTUNE = 1
 
 # (name, restype, argtypes) of every function include/corr.h declares

@@ -42,6 +42,7 @@ struct corr_ctx {
   int smem_bytes, z_stages, pk_stages;
   uint32_t z_stage_bytes, pk_stage_bytes;
   int tm;  // 1: the TMEM-operand kernel (xengine_tm.cu) runs this context's launches
+  int pair;  // 1: CTA pairs (the quad cover, M = 256 MMAs) run this context's launches
   int pitch;           // row pitch of the staged block (block_len rounded up to 16)
   uint8_t *d_pitched;  // [n_chan][n_in][pitch] when block_len % 16 != 0
   uint8_t *d_turned;   // [n_chan][n_in][pitch]: corner-turned blocks (allocated on first use)
@@ -111,8 +112,19 @@ int free_ctx(corr_ctx *ctx) {
 bool use_tm_kernel(int n_in) {
   const char *e = std::getenv("CORR_CMAC_KERNEL");
   if (e && std::strcmp(e, "tm") == 0) return true;
-  if (e && std::strcmp(e, "smem") == 0) return false;
+  if (e && (std::strcmp(e, "smem") == 0 || std::strcmp(e, "pair") == 0)) return false;
   return n_in > xe::kTileInputs && n_in <= 2 * xe::kTileInputs;
+}
+
+// Whether CTA pairs run a context of n_in inputs (more than 256 only).  The
+// pair's shared B operand halves the inputs each SM unpacks per MMA, but on
+// this part the pair kernel measured 5 % slower per issued MAC than one-CTA
+// units at 512 to 2048 inputs, and its cover issues more padding on the
+// diagonal: it runs only when CORR_CMAC_KERNEL=pair asks for it.
+bool use_pair_kernel(int n_in) {
+  if (n_in <= 256) return false;
+  const char *e = std::getenv("CORR_CMAC_KERNEL");
+  return e && std::strcmp(e, "pair") == 0;
 }
 
 // Shared-memory stages of the TMEM-operand kernel for n_in inputs: operand
@@ -212,7 +224,9 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
     if (ms > 0) ctx->timeout_ns = (unsigned long long)ms * 1000000ull;
   }
 
-  std::vector<XUnit> units = xe::build_schedule(ctx->n_in);
+  ctx->pair = use_pair_kernel(ctx->n_in) ? 1 : 0;
+  std::vector<XUnit> units =
+      xe::build_schedule(ctx->n_in, ctx->pair ? xe::kCoverQuads : xe::kCoverWindow);
   if (units.empty()) {
     free_ctx(ctx);
     return CORR_EINVAL;
@@ -288,11 +302,24 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
     free_ctx(ctx);
     return rc;
   }
+  // workers: CTAs, or for CTA pairs the clusters that fit at once
+  int workers = ctx->n_sm;
+  if (ctx->pair) {
+    if ((rc = cuda_err(xe::cmac_set_smem(smem_optin))) != CORR_OK) {
+      free_ctx(ctx);
+      return rc;
+    }
+    workers = std::min(ctx->n_sm / 2, xe::cmac_pair_clusters(ctx->smem_bytes));
+    if (workers < 1) {
+      free_ctx(ctx);
+      return CORR_ECUDA;
+    }
+  }
   for (int nb = 1; nb <= ctx->per_launch; ++nb) {
     std::vector<xe::XItem> items;
     std::vector<int> first;
     ItemPlan &pl = ctx->plans[nb];
-    pl.grid = xe::build_items({{&plan_units, n_chan, block_len, nb}}, ctx->n_sm, items, first);
+    pl.grid = xe::build_items({{&plan_units, n_chan, block_len, nb}}, workers, items, first);
     if ((rc = cuda_err(cudaMalloc(&pl.d_items, items.size() * sizeof(xe::XItem)))) != CORR_OK ||
         (rc = cuda_err(cudaMalloc(&pl.d_cta_first, first.size() * sizeof(int)))) != CORR_OK ||
         (rc = cuda_err(cudaMemcpy(pl.d_items, items.data(), items.size() * sizeof(xe::XItem),
@@ -352,8 +379,10 @@ int launch_staged(corr_ctx *ctx, const uint8_t *const *staged, int nb, cudaStrea
   const ItemPlan &pl = ctx->plans[nb];
   p.items = pl.d_items;
   p.cta_first = pl.d_cta_first;
-  if ((rc = cuda_err(ctx->tm ? xe::launch_cmac_tm(maps, p, pl.grid, ctx->smem_bytes, st)
-                            : xe::launch_cmac(maps, p, pl.grid, ctx->smem_bytes, st))) != CORR_OK)
+  if ((rc = cuda_err(ctx->tm     ? xe::launch_cmac_tm(maps, p, pl.grid, ctx->smem_bytes, st)
+                     : ctx->pair ? xe::launch_cmac_pair(maps, p, pl.grid, ctx->smem_bytes, st)
+                                 : xe::launch_cmac(maps, p, pl.grid, ctx->smem_bytes, st))) !=
+      CORR_OK)
     return rc;
   ctx->launches++;
   if (!selftest_timeout_ns) {
@@ -436,7 +465,8 @@ int corr_push_block_tcn(corr_ctx *ctx, const uint8_t *d_src, void *stream) {
   // The shared-memory kernel stages F-engine-order blocks directly (TMA boxes
   // of [128 samples][64 inputs], transposed on chip) when the block's strides
   // allow a tensor map; otherwise the block is turned in HBM first.
-  if (!ctx->tm && ctx->n_in % 16 == 0 && (reinterpret_cast<uintptr_t>(d_src) & 15u) == 0)
+  if (!ctx->tm && !ctx->pair && ctx->n_in % 16 == 0 &&
+      (reinterpret_cast<uintptr_t>(d_src) & 15u) == 0)
     return launch_staged(ctx, &d_src, 1, st, 0, true);
   int rc;
   if (!ctx->d_turned &&
@@ -574,8 +604,9 @@ int corr_plan_items(int n_in, int n_chan, int block_len, int n_blocks, int cover
                     int *items, int cap, int *n_items, int *cta_first, int *used_grid) {
   if (n_in <= 0 || n_in > CORR_MAX_INPUTS || n_chan <= 0 || block_len <= 0 ||
       block_len > CORR_MAX_BLOCK_LEN || n_blocks <= 0 || n_blocks > xe::kMaxBlocksPerLaunch ||
-      grid <= 0 || cover < 0 || cover > 2)
+      grid <= 0 || cover < 0 || cover > 3)
     return CORR_EINVAL;
+  // with CORR_COVER_QUADS, grid counts CTA pairs
   const std::vector<XUnit> units = xe::build_schedule(n_in, cover);
   if (units.empty()) return CORR_EINVAL;
   std::vector<xe::XItem> it;
@@ -600,30 +631,33 @@ int corr_plan_items(int n_in, int n_chan, int block_len, int n_blocks, int cover
 
 int corr_plan_cover(int n_in, int cover_kind, uint8_t *cover, int *n_units,
                     long long *issued_cmacs) {
-  if (n_in <= 0 || n_in > CORR_MAX_INPUTS || cover_kind < 0 || cover_kind > 2) return CORR_EINVAL;
+  if (n_in <= 0 || n_in > CORR_MAX_INPUTS || cover_kind < 0 || cover_kind > 3) return CORR_EINVAL;
   std::vector<XUnit> units = xe::build_schedule(n_in, cover_kind);
   if (units.empty()) return CORR_EINVAL;
   long long issued = 0;
   for (const XUnit &u : units) {
     // a unit of several channels repeats its cover once per channel: count
     // the first channel's segments
-    for (int sg = 0; sg < u.n_seg; ++sg) {
-      const XSeg &s = u.seg[sg];
-      if (s.chan_off != 0) continue;
-      issued += 64LL * s.n;  // 128 accumulator rows = 64 inputs x (re, im)
-      if (!cover) continue;
-      // the epilogue's mapping: lane rho holds input row_in0 + 8 (rho / 16) + rho % 8,
-      // real part when (rho / 8) is even; column n holds input col_in0 + n
-      for (int rho = 0; rho < 128; ++rho) {
-        if ((rho >> 3) & 1) continue;
-        const int i = s.row_in0 + 8 * (rho >> 4) + (rho & 7);
-        if (i >= n_in) continue;
-        for (int n = 0; n < s.n; ++n) {
-          const int j = s.col_in0 + n;
-          if (j <= i) cover[(size_t)i * n_in + j]++;
+    // a pair unit covers its rows once per CTA of the pair, the odd CTA's
+    // pair_rows inputs further on
+    for (int rank = 0; rank < (u.pair_rows ? 2 : 1); ++rank)
+      for (int sg = 0; sg < u.n_seg; ++sg) {
+        const XSeg &s = u.seg[sg];
+        if (s.chan_off != 0) continue;
+        issued += 64LL * s.n;  // 128 accumulator rows = 64 inputs x (re, im)
+        if (!cover) continue;
+        // the epilogue's mapping: lane rho holds input row_in0 + 8 (rho / 16) + rho % 8,
+        // real part when (rho / 8) is even; column n holds input col_in0 + n
+        for (int rho = 0; rho < 128; ++rho) {
+          if ((rho >> 3) & 1) continue;
+          const int i = s.row_in0 + rank * u.pair_rows + 8 * (rho >> 4) + (rho & 7);
+          if (i >= n_in) continue;
+          for (int n = 0; n < s.n; ++n) {
+            const int j = s.col_in0 + n;
+            if (j <= i) cover[(size_t)i * n_in + j]++;
+          }
         }
       }
-    }
   }
   if (n_units) *n_units = (int)units.size();
   if (issued_cmacs) *issued_cmacs = issued;

@@ -70,6 +70,12 @@ struct XSeg {
 struct XUnit {
   int n_reg, n_seg;
   int n_chan;    // channels one unit covers (its regions and segments name the offsets)
+  // 0: one CTA runs the unit.  kPairRows: a CTA pair runs it with M = 256
+  // MMAs; the regions and segments describe the even CTA, and the odd CTA
+  // stages and owns the rows kPairRows inputs further on (its regions'
+  // in_lo and its segments' row_in0 + kPairRows; col_in0 is shared, since
+  // the pair's B operand is the even CTA's B rows followed by the odd one's)
+  int pair_rows;
   int z_rows;    // rows staged per chunk (sum over regions)
   int pk_bytes;  // packed bytes per chunk (sum over regions)
   int work;      // relative MMA work (sum of n), for ordering
@@ -98,6 +104,10 @@ struct XProb {
 struct XItem {
   int prob, tpl, chan, pk0, npk;
 };
+
+// Inputs per CTA of a pair unit: two row tiles, and half of a 256-column
+// B operand.
+constexpr int kPairRows = 128;
 
 // Bits of the device status word.
 constexpr int kStatusTimeout = 1;  // a bounded wait ran out
@@ -212,6 +222,13 @@ cudaError_t launch_cmac(const XMaps &maps, const XParams &p, int grid, int smem_
 cudaError_t launch_cmac_batch(const XBatchMaps &maps, const XParams &p, int grid, int smem_bytes,
                               cudaStream_t stream);
 cudaError_t cmac_set_smem(int smem_bytes);
+// The CTA-pair instance for units with pair_rows != 0: `clusters` clusters
+// of two CTAs, cluster w running items [cta_first[w], cta_first[w + 1]).
+cudaError_t launch_cmac_pair(const XMaps &maps, const XParams &p, int clusters, int smem_bytes,
+                             cudaStream_t stream);
+// Clusters of two CTAs of the pair instance that can be resident at once
+// (0 if the query fails).
+int cmac_pair_clusters(int smem_bytes);
 cudaError_t launch_cmac_tm(const XMaps &maps, const XParams &p, int grid, int smem_bytes,
                            cudaStream_t stream);
 cudaError_t cmac_tm_set_smem(int smem_bytes);

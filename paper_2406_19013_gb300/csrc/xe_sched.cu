@@ -108,6 +108,28 @@ std::vector<XUnit> build_schedule(int N, int cover) {
       add_seg(u, 128 * t, 0, 2048, std::min(kTileInputs * (t + 1), n16), kTileInputs * t, 0);
       units.push_back(u);
     }
+  } else if (N > 256 && cover == kCoverQuads) {
+    // CTA pairs: rows [R, R + 256) (the even CTA R .. R + 127, the odd one
+    // R + 128 .. R + 255) against columns [P, P + 256), P <= R.  Below the
+    // diagonal the B rows are a plain region (P .. P + 127 on the even CTA,
+    // P + 128 .. on the odd one); on it they are the CTA's own interleaved
+    // A rows.
+    for (int R = 0; R < N; R += 2 * kPairRows) {
+      for (int P = 0; P <= R; P += 2 * kPairRows) {
+        XUnit u = empty_unit();
+        u.pair_rows = kPairRows;
+        add_reg(u, R, kPairRows, 1);
+        int bz = 0, sbo = 2048;
+        if (P < R) {
+          add_reg(u, P, kPairRows, 0);
+          bz = u.reg[1].z_row;
+          sbo = 1024;
+        }
+        for (int t = 0; t < 2; ++t)
+          add_seg(u, 128 * t, bz, sbo, 2 * kPairRows, R + kTileInputs * t, P);
+        units.push_back(u);
+      }
+    }
   } else {
     // pairs of row tiles (2m, 2m+1) against 256-column pieces of their strip
     for (int m = 0; 2 * m < n_rt; ++m) {
@@ -162,13 +184,18 @@ bool stage_layout(const std::vector<const std::vector<XUnit> *> &unit_sets, int 
   const int avail = smem_optin - fixed;
   const int zb = (int)L.z_stage_bytes, pb = (int)L.pk_stage_bytes;
   const int zcap = std::min(max_z, kMaxZStages);
-  // Operand stages first (three if they fit beside three packed stages, else
-  // two beside two), then packed stages (bytes in flight from HBM) up to six,
+  // Operand stages first (three beside three packed stages, else three
+  // beside two, else two beside three or two), then packed stages (bytes in
+  // flight from HBM) up to six,
   // operand stages up to four, and both up to their caps while they fit.
   int zs, ps;
   if (3 * zb + 3 * pb <= avail && zcap >= 3) {
     zs = 3;
     ps = 3;
+  } else if (3 * zb + 2 * pb <= avail && zcap >= 3) {
+    // (the CTA-pair units: a third operand stage hides the peer's arrivals)
+    zs = 3;
+    ps = 2;
   } else if (2 * zb + 3 * pb <= avail) {
     zs = 2;
     ps = 3;

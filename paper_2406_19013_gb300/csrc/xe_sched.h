@@ -17,8 +17,12 @@ enum Cover {
   // N <= 256: one unit per row tile t, staging inputs [0, 64 (t + 1)) only.
   kCoverStrips = 1,
   // any N: pairs of row tiles against 256-column pieces of their strip
-  // (the only cover for N > 256).
+  // (the only one-CTA cover for N > 256).
   kCoverPairs = 2,
+  // N > 256, CTA pairs: blocks of 256 rows (four row tiles, two per CTA)
+  // against 256-column pieces of their strip, each piece's B rows split
+  // between the two CTAs (units with pair_rows = kPairRows).
+  kCoverQuads = 3,
 };
 
 // Templates of the cover, heaviest first.  kCoverWindow and kCoverStrips

@@ -42,6 +42,21 @@ __device__ __forceinline__ void decode_word(uint32_t w, uint2 &a, uint2 &q) {
   q = make_uint2(__byte_perm(im02, nre02, 0x7531), __byte_perm(im13, nre13, 0x7531));
 }
 
+// As decode_word, the A-row piece only (for plain regions, whose inputs are
+// only ever columns): the negations and the Q-row permutes are skipped.
+__device__ __forceinline__ void decode_word_a(uint32_t w, uint2 &a) {
+  const uint32_t s16 = 0x2C002C00u, m72 = 0xD480D480u;    // (1/16, 1/16), (-72, -72)
+  const uint32_t one = 0x3C003C00u, m1032 = 0xE408E408u;  // (1, 1), (-1032, -1032)
+  const uint32_t w8 = w >> 8;
+  const uint32_t lo02 = (w & 0x000F000Fu) ^ 0x64086408u;
+  const uint32_t hi02 = (w & 0x00F000F0u) ^ 0x64806480u;
+  const uint32_t lo13 = (w8 & 0x000F000Fu) ^ 0x64086408u;
+  const uint32_t hi13 = (w8 & 0x00F000F0u) ^ 0x64806480u;
+  const uint32_t re02 = hfma2_bits(hi02, s16, m72), im02 = hfma2_bits(lo02, one, m1032);
+  const uint32_t re13 = hfma2_bits(hi13, s16, m72), im13 = hfma2_bits(lo13, one, m1032);
+  a = make_uint2(__byte_perm(re02, im02, 0x7531), __byte_perm(re13, im13, 0x7531));
+}
+
 // 16-byte shared-memory load and store on a 32-bit shared address.  The
 // operand buffers are carved from the dynamic shared memory by integer
 // alignment, so plain pointers into them would be generic pointers; these

@@ -38,6 +38,8 @@
 // frees TMEM and reports through *status.
 #include <cuda.h>
 
+#include <cstring>
+
 #include "ptx.cuh"
 #include "xe_internal.h"
 #include "xe_unpack.cuh"
@@ -74,7 +76,10 @@ __device__ __forceinline__ int chunks_in_pk(const XProb &pb, int kc) {
 // TCN: the blocks are in F-engine order (XParams::tcn), staged and unpacked
 // by the transposing path; a compile-time choice, so that the X-engine-order
 // kernel carries none of that code.
-template <int M, bool TCN>
+// PAIR: the launch is clusters of two CTAs running pair units (XUnit::
+// pair_rows): both CTAs stage and unpack their own rows, the even CTA's
+// issuers run M = 256 MMAs over both, and both fold their own TMEM rows.
+template <int M, bool TCN, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     xengine_cmac_kernel(const __grid_constant__ XMapsT<M> maps, const XParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -108,29 +113,40 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(b.pk_empty + 8 * s, kUnpackWarps);
     }
     for (int s = 0; s < p.z_stages; ++s) {
-      mbar_init(b.z_full + 8 * s, kUnpackWarps);
+      mbar_init(b.z_full + 8 * s, PAIR ? 2 * kUnpackWarps : kUnpackWarps);
       mbar_init(b.z_empty + 8 * s, kMmaWarps);
     }
     mbar_init(b.acc_full, kMmaWarps);
-    mbar_init(b.acc_empty, kEpiWarps);
+    mbar_init(b.acc_empty, PAIR ? 2 * kEpiWarps : kEpiWarps);
     for (int m = 0; m < kMmaWarps; ++m) mbar_init(b.drain + 8 * m, 1);
     mbar_init(b.never, 1);  // nothing ever arrives here
     *abort_flag = 0;
     fence_mbar_init();
   }
   if (warp == kWarpMma0) {
-    tmem_alloc(smem_u32(misc), kTmemCols);
-    tmem_relinquish();
+    if (PAIR) {
+      tmem_alloc_pair(smem_u32(misc), kTmemCols);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(misc), kTmemCols);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
+  // a pair's CTAs arrive on each other's barriers: both must be initialised
+  if (PAIR) cluster_sync();
   tc_fence_after();
   const uint32_t tmem = misc[0];
+  // rank in the pair, and the rows of the odd CTA's share of a pair unit
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  const int rank_rows = PAIR ? kPairRows * (int)rank : 0;
 
   int it0, it1, it_step;
   if (p.items) {
-    it0 = p.cta_first[blockIdx.x];
-    it1 = p.cta_first[blockIdx.x + 1];
+    const int wkr = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;  // cluster or CTA
+    it0 = p.cta_first[wkr];
+    it1 = p.cta_first[wkr + 1];
     it_step = 1;
   } else {
     it0 = blockIdx.x;
@@ -167,7 +183,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           armed_ph[s] = ph;
           const uint32_t dst0 = smem_u32(pk_buf + (size_t)s * p.pk_stage_bytes);
           for (int r = 0; r < n_reg; ++r) {
-            const int in_lo = u->reg[r].in_lo, n_in = u->reg[r].n_in, off = u->reg[r].pk_off;
+            const int in_lo = u->reg[r].in_lo + rank_rows, n_in = u->reg[r].n_in;
+            const int off = u->reg[r].pk_off;
             const int ch = item.chan + u->reg[r].chan_off;  // past the last: zero fill
             for (int bx = 0; bx < n_in; bx += kTileInputs) {
               if (TCN)  // (input, channel, time): a [128 samples][64 inputs] box
@@ -192,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // thread per warp, so independent accumulators are fed by parallel
     // instruction streams.
     const int m = warp - kWarpMma0;
-    if (lane == 0) {
+    if (lane == 0 && (!PAIR || rank == 0)) {  // a pair's MMAs issue from its even CTA
       int zs = 0;
       uint32_t zph = 0;
       long long nu = 0;
@@ -217,18 +234,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < 2; ++j) {
           const XSeg &sgm = u->seg[j < n_mine ? m + kMmaWarps * j : 0];
           d_col[j] = tmem + (uint32_t)sgm.tmem_col;
-          idesc[j] = idesc_e5m2_f32(128, sgm.n);
+          idesc[j] = idesc_e5m2_f32(PAIR ? 256 : 128, sgm.n);
           a_lo[j] = sdesc_sw128_lo(z0 + (uint32_t)sgm.a_zrow * 128u);
           b_lo[j] = sdesc_sw128_lo(z0 + (uint32_t)sgm.b_zrow * 128u);
           b_hi[j] = sdesc_sw128_hi((uint32_t)sgm.b_sbo);
         }
-        if (nu > 0 && !mbar_wait(b.acc_empty, (uint32_t)((nu - 1) & 1), abort_flag, to)) break;
+        if (nu > 0 &&
+            !(PAIR ? mbar_wait_cluster(b.acc_empty, (uint32_t)((nu - 1) & 1), abort_flag, to)
+                   : mbar_wait(b.acc_empty, (uint32_t)((nu - 1) & 1), abort_flag, to)))
+          break;
         tc_fence_after();
         uint32_t acc0 = 0;  // the item's first MMA of each accumulator overwrites it
         for (int k = item.pk0; k < item.pk0 + item.npk && ok; ++k) {
           const int nch = chunks_in_pk(pb, k % pb.pk_per_block);
           for (int sub = 0; sub < nch; ++sub) {
-            if (!mbar_wait(b.z_full + 8 * zs, zph, abort_flag, to)) { ok = false; break; }
+            if (!(PAIR ? mbar_wait_cluster(b.z_full + 8 * zs, zph, abort_flag, to)
+                       : mbar_wait(b.z_full + 8 * zs, zph, abort_flag, to))) {
+              ok = false;
+              break;
+            }
             tc_fence_after();
             const uint32_t zoff = ((uint32_t)zs * p.z_stage_bytes) >> 4;
 #pragma unroll
@@ -236,19 +260,35 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (j >= n_mine) break;
               const uint32_t al = a_lo[j] + zoff, bl = b_lo[j] + zoff;
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
-                mma_f8_ss_w(d_col[j], al + 2u * kk, a_hi, bl + 2u * kk, b_hi[j], idesc[j],
-                            kk ? 1u : acc0);
+              for (int kk = 0; kk < 4; ++kk) {
+                if (PAIR)
+                  mma_f8_ss_w_pair(d_col[j], al + 2u * kk, a_hi, bl + 2u * kk, b_hi[j], idesc[j],
+                                   kk ? 1u : acc0);
+                else
+                  mma_f8_ss_w(d_col[j], al + 2u * kk, a_hi, bl + 2u * kk, b_hi[j], idesc[j],
+                              kk ? 1u : acc0);
+              }
             }
             acc0 = 1;
-            mma_commit(b.z_empty + 8 * zs);
+            if (PAIR)
+              mma_commit_pair(b.z_empty + 8 * zs, 3);  // both CTAs' operand stages
+            else
+              mma_commit(b.z_empty + 8 * zs);
             if (++zs == p.z_stages) { zs = 0; zph ^= 1u; }
           }
         }
-        if (ok) mma_commit(b.acc_full);
+        if (ok) {
+          if (PAIR)
+            mma_commit_pair(b.acc_full, 3);
+          else
+            mma_commit(b.acc_full);
+        }
       }
       // all MMAs this thread issued complete before TMEM is released
-      mma_commit(b.drain + 8 * m);
+      if (PAIR)
+        mma_commit_pair(b.drain + 8 * m, 1);
+      else
+        mma_commit(b.drain + 8 * m);
       int dummy = 0;
       mbar_wait(b.drain + 8 * m, 0, &dummy, to);
     }
@@ -360,18 +400,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int kr = 0; kr < 2; ++kr) {
               if (kr >= n_k[r]) break;
               const uint4 in = kr == 0 ? in0 : in1;
-              uint2 a0, q0, a1, q1, a2, q2, a3, q3;
-              decode_word(in.x, a0, q0);
-              decode_word(in.y, a1, q1);
-              decode_word(in.z, a2, q2);
-              decode_word(in.w, a3, q3);
               const uint32_t d0 = dst + (kr ? dst_step[r] : 0u) + off0;
               const uint32_t d1 = dst + (kr ? dst_step[r] : 0u) + off1;
-              sts128(d0, a0.x, a0.y, a1.x, a1.y);
-              sts128(d1, a2.x, a2.y, a3.x, a3.y);
-              if (il[r]) {  // the Q rows follow 8 rows (1024 bytes) after the A rows
+              if (il[r]) {
+                uint2 a0, q0, a1, q1, a2, q2, a3, q3;
+                decode_word(in.x, a0, q0);
+                decode_word(in.y, a1, q1);
+                decode_word(in.z, a2, q2);
+                decode_word(in.w, a3, q3);
+                sts128(d0, a0.x, a0.y, a1.x, a1.y);
+                sts128(d1, a2.x, a2.y, a3.x, a3.y);
+                // the Q rows follow 8 rows (1024 bytes) after the A rows
                 sts128_q(d0, q0.x, q0.y, q1.x, q1.y);
                 sts128_q(d1, q2.x, q2.y, q3.x, q3.y);
+              } else {
+                uint2 a0, a1, a2, a3;
+                decode_word_a(in.x, a0);
+                decode_word_a(in.y, a1);
+                decode_word_a(in.z, a2);
+                decode_word_a(in.w, a3);
+                sts128(d0, a0.x, a0.y, a1.x, a1.y);
+                sts128(d1, a2.x, a2.y, a3.x, a3.y);
               }
             }
           }
@@ -379,7 +428,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) {
-            mbar_arrive(b.z_full + 8 * zs);
+            if (PAIR && rank != 0)
+              mbar_arrive_cluster(b.z_full + 8 * zs, 0);  // the issuers are on the even CTA
+            else
+              mbar_arrive(b.z_full + 8 * zs);
             if (sub == nch - 1) mbar_arrive(b.pk_empty + 8 * s);
           }
           if (++zs == p.z_stages) { zs = 0; zph ^= 1u; }
@@ -416,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const XSeg sgm = u->seg[sg];
         const int c = item.chan + sgm.chan_off;
         if (c >= pb.n_chan) continue;  // a two-channel unit's missing last channel
-        const int i = sgm.row_in0 + 8 * g + l_in;
+        const int i = sgm.row_in0 + rank_rows + 8 * g + l_in;
         const bool row_ok = i < pb.n_in;
         int64_t *arow = pb.acc + ((long long)c * pb.n_pairs + (long long)i * (i + 1) / 2) * 2;
         const long long acc_elems = (long long)pb.n_chan * pb.n_pairs * 2;
@@ -460,43 +512,93 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(b.acc_empty);
+      if (lane == 0) {
+        if (PAIR && rank != 0)
+          mbar_arrive_cluster(b.acc_empty, 0);
+        else
+          mbar_arrive(b.acc_empty);
+      }
     }
   }
 
   tc_fence_before();
   __syncthreads();
+  // a pair's even CTA reads the odd one's operands and the odd one arrives on
+  // the even one's barriers: neither leaves before both are done
+  if (PAIR) cluster_sync();
   if (warp == kWarpMma0) {
     __syncwarp();
     tc_fence_after();
-    tmem_dealloc(tmem, kTmemCols);
+    if (PAIR)
+      tmem_dealloc_pair(tmem, kTmemCols);
+    else
+      tmem_dealloc(tmem, kTmemCols);
   }
   if (threadIdx.x == 0 && *abort_flag) atomicOr(p.status, 1);
 }
 
 cudaError_t cmac_set_smem(int smem_bytes) {
-  cudaError_t e = cudaFuncSetAttribute(xengine_cmac_kernel<kMaxMaps, false>,
+  cudaError_t e = cudaFuncSetAttribute(xengine_cmac_kernel<kMaxMaps, false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(xengine_cmac_kernel<kMaxMaps, true>,
+  e = cudaFuncSetAttribute(xengine_cmac_kernel<kMaxMaps, true, false>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(xengine_cmac_kernel<kMaxBatchMaps, false>,
+  e = cudaFuncSetAttribute(xengine_cmac_kernel<kMaxMaps, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(xengine_cmac_kernel<kMaxBatchMaps, false, false>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
 }
 
 cudaError_t launch_cmac(const XMaps &maps, const XParams &p, int grid, int smem_bytes,
                         cudaStream_t stream) {
   if (p.tcn)
-    xengine_cmac_kernel<kMaxMaps, true><<<grid, kThreads, smem_bytes, stream>>>(maps, p);
+    xengine_cmac_kernel<kMaxMaps, true, false><<<grid, kThreads, smem_bytes, stream>>>(maps, p);
   else
-    xengine_cmac_kernel<kMaxMaps, false><<<grid, kThreads, smem_bytes, stream>>>(maps, p);
+    xengine_cmac_kernel<kMaxMaps, false, false><<<grid, kThreads, smem_bytes, stream>>>(maps, p);
   return cudaGetLastError();
+}
+
+namespace {
+// Launch configuration of the pair instance: clusters of two CTAs.
+struct PairConfig {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  PairConfig(int clusters, int smem_bytes, cudaStream_t stream) {
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(2 * clusters);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = (size_t)smem_bytes;
+    cfg.stream = stream;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+};
+}  // namespace
+
+cudaError_t launch_cmac_pair(const XMaps &maps, const XParams &p, int clusters, int smem_bytes,
+                             cudaStream_t stream) {
+  PairConfig c(clusters, smem_bytes, stream);
+  return cudaLaunchKernelEx(&c.cfg, xengine_cmac_kernel<kMaxMaps, false, true>, maps, p);
+}
+
+int cmac_pair_clusters(int smem_bytes) {
+  PairConfig c(1, smem_bytes, nullptr);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, xengine_cmac_kernel<kMaxMaps, false, true>, &c.cfg) !=
+      cudaSuccess)
+    return 0;
+  return n;
 }
 
 cudaError_t launch_cmac_batch(const XBatchMaps &maps, const XParams &p, int grid, int smem_bytes,
                               cudaStream_t stream) {
-  xengine_cmac_kernel<kMaxBatchMaps, false><<<grid, kThreads, smem_bytes, stream>>>(maps, p);
+  xengine_cmac_kernel<kMaxBatchMaps, false, false><<<grid, kThreads, smem_bytes, stream>>>(maps, p);
   return cudaGetLastError();
 }
 

@@ -91,8 +91,9 @@ def test_plan_rejects(corr):
         corr.plan(8193)
 
 
-@pytest.mark.parametrize("cover", [0, 1, 2])
-@pytest.mark.parametrize("n", [1, 16, 40, 64, 65, 127, 128, 192, 200, 256, 257, 512, 1000])
+@pytest.mark.parametrize("cover", [0, 1, 2, 3])
+@pytest.mark.parametrize("n", [1, 16, 40, 64, 65, 127, 128, 192, 200, 256, 257, 300, 384, 512,
+                               600, 1000, 1024, 2048])
 def test_every_cover_covers_lower_triangle_once(corr, n, cover):
     _, issued, got = corr.plan_cover(n, cover, with_cover=True)
     assert np.array_equal(got, np.tril(np.ones((n, n), dtype=np.uint8)))
@@ -168,13 +169,30 @@ def test_item_split_other_covers(corr, cover):
     _check_split(corr, 192, 300, 4096, 2, 152, cover)
 
 
+@pytest.mark.parametrize("args", [(2048, 4, 4096, 2, 76), (1000, 300, 8192, 1, 76),
+                                  (512, 16, 16384, 1, 76)])
+def test_item_split_quad_cover(corr, args):
+    """With CTA pairs the items are dealt to clusters (76 on 152 SMs)."""
+    _check_split(corr, *args, cover=3)
+
+
+def test_quad_cover_units_are_pair_units(corr):
+    """Each quad unit's 256 rows are covered by its two CTAs: the cover view
+    counts the odd CTA's rows 128 inputs further on, and 2048 inputs need 36
+    units (8 row blocks x up to 8 column pieces), 8 of them on the diagonal."""
+    n_units, issued, got = corr.plan_cover(2048, 3, with_cover=True)
+    assert n_units == 36
+    assert issued == 36 * 2 * 2 * 64 * 256  # units x CTAs x row tiles x 64 inputs x 256 columns
+    assert np.array_equal(got, np.tril(np.ones((2048, 2048), dtype=np.uint8)))
+
+
 def test_plan_items_rejects(corr):
     with pytest.raises(corr.CorrError):
         corr.plan_items(192, 10, 8192, 17, 152)  # 17 x 8192 samples exceed one fold
     with pytest.raises(corr.CorrError):
         corr.plan_items(192, 10, 8192, 1, 0)
     with pytest.raises(corr.CorrError):
-        corr.plan_items(192, 10, 8192, 1, 152, cover=3)
+        corr.plan_items(192, 10, 8192, 1, 152, cover=4)
 
 
 def test_tuned_cover_is_empty_without_a_gpu(corr):

@@ -471,3 +471,27 @@ def test_both_cmac_kernels_match_oracle(corr, torch_cuda, oracle_mod, synth_mod,
     assert np.array_equal(vis, ov)
     if n_pol == 2:
         assert np.array_equal(st, ost)
+
+
+@pytest.mark.parametrize("kernel", ["pair", "smem"])
+@pytest.mark.parametrize("n_ant,n_pol,C,T,nb", [
+    (150, 2, 2, 2048, 2),    # N = 300: the odd CTA of the last row block is empty
+    (256, 2, 3, 1024, 2),    # N = 512: two row blocks, one piece below the diagonal
+    (300, 2, 2, 1008, 2),    # N = 600: ragged inputs and a ragged last chunk
+    (512, 2, 2, 512, 3),     # N = 1024: four row blocks
+])
+def test_cta_pair_kernel_matches_oracle(corr, torch_cuda, oracle_mod, synth_mod, monkeypatch,
+                                        kernel, n_ant, n_pol, C, T, nb):
+    # CORR_CMAC_KERNEL=pair runs contexts of more than 256 inputs on CTA
+    # pairs (the quad cover: M = 256 MMAs whose B rows are split between the
+    # two CTAs of a cluster); =smem on one-CTA pairs units.  Both must give
+    # the oracle's visibilities and Stokes products exactly.
+    monkeypatch.setenv("CORR_CMAC_KERNEL", kernel)
+    N = n_ant * n_pol
+    tones = synth_mod.random_phase_tone(N, 23)
+    blocks = [synth_mod.make_block(N, C, T, seed=500 + N, block=b, tones=tones) for b in range(nb)]
+    blocks[0][:, :, : T // 2] = 0x88  # -8-8j runs: the largest products
+    vis, st = _run(corr, torch_cuda, blocks, n_ant, n_pol)
+    ov, ost = _oracle(oracle_mod, blocks, n_ant, n_pol)
+    assert np.array_equal(vis, ov)
+    assert np.array_equal(st, ost)
