@@ -108,6 +108,9 @@ struct XItem {
 // Inputs per CTA of a pair unit: two row tiles, and half of a 256-column
 // B operand.
 constexpr int kPairRows = 128;
+// A pair unit has two segments (one per row tile of each CTA), each with
+// its own issuing thread on the even CTA.
+constexpr int kPairIssuers = 2;
 
 // Bits of the device status word.
 constexpr int kStatusTimeout = 1;  // a bounded wait ran out

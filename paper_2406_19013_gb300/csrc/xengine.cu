@@ -113,10 +113,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(b.pk_empty + 8 * s, kUnpackWarps);
     }
     for (int s = 0; s < p.z_stages; ++s) {
-      mbar_init(b.z_full + 8 * s, PAIR ? 2 * kUnpackWarps : kUnpackWarps);
-      mbar_init(b.z_empty + 8 * s, kMmaWarps);
+      // a pair's even CTA also counts the odd CTA's forwarded arrive
+      mbar_init(b.z_full + 8 * s, (PAIR && cluster_ctarank() == 0) ? kUnpackWarps + 1 : kUnpackWarps);
+      mbar_init(b.z_empty + 8 * s, PAIR ? kPairIssuers : kMmaWarps);
     }
-    mbar_init(b.acc_full, kMmaWarps);
+    mbar_init(b.acc_full, PAIR ? kPairIssuers : kMmaWarps);
     mbar_init(b.acc_empty, PAIR ? 2 * kEpiWarps : kEpiWarps);
     for (int m = 0; m < kMmaWarps; ++m) mbar_init(b.drain + 8 * m, 1);
     mbar_init(b.never, 1);  // nothing ever arrives here
@@ -209,7 +210,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // thread per warp, so independent accumulators are fed by parallel
     // instruction streams.
     const int m = warp - kWarpMma0;
-    if (lane == 0 && (!PAIR || rank == 0)) {  // a pair's MMAs issue from its even CTA
+    // a pair's MMAs issue from its even CTA, one issuer per segment
+    if (lane == 0 && (!PAIR || (rank == 0 && m < kPairIssuers))) {
       int zs = 0;
       uint32_t zph = 0;
       long long nu = 0;
@@ -291,6 +293,28 @@ __global__ void __launch_bounds__(kThreads, 1)
         mma_commit(b.drain + 8 * m);
       int dummy = 0;
       mbar_wait(b.drain + 8 * m, 0, &dummy, to);
+    }
+    if (PAIR && rank != 0 && m == 0 && lane == 0) {
+      // The odd CTA's operand stages are announced to the even CTA's
+      // issuers by this one thread: it waits for the local unpack warps'
+      // arrivals, then makes a single cluster-scope release-arrive on the
+      // even CTA's z_full (one cluster fence per chunk instead of one per
+      // unpack warp).
+      int zs = 0;
+      uint32_t zph = 0;
+      bool ok = true;
+      for (int it = it0; it < it1 && ok && !*abort_flag; it += it_step) {
+        const XItem item = item_at(p, it);
+        const XProb pb = p.probs[item.prob];
+        for (int k = item.pk0; k < item.pk0 + item.npk && ok; ++k) {
+          const int nch = chunks_in_pk(pb, k % pb.pk_per_block);
+          for (int sub = 0; sub < nch; ++sub) {
+            if (!mbar_wait(b.z_full + 8 * zs, zph, abort_flag, to)) { ok = false; break; }
+            mbar_arrive_cluster(b.z_full + 8 * zs, 0);
+            if (++zs == p.z_stages) { zs = 0; zph ^= 1u; }
+          }
+        }
+      }
     }
   } else if (warp < kUnpackWarps) {
     // ------------------------------------------------------------ unpack
@@ -428,10 +452,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) {
-            if (PAIR && rank != 0)
-              mbar_arrive_cluster(b.z_full + 8 * zs, 0);  // the issuers are on the even CTA
-            else
-              mbar_arrive(b.z_full + 8 * zs);
+            mbar_arrive(b.z_full + 8 * zs);
             if (sub == nch - 1) mbar_arrive(b.pk_empty + 8 * s);
           }
           if (++zs == p.z_stages) { zs = 0; zph ^= 1u; }
