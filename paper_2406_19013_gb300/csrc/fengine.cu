@@ -66,14 +66,49 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 
 // Forward 4-point DFT in place: X[k] = sum_n a[n] (-i)^(n k).
+// Complex sum and difference as one packed two-lane fp32 instruction each
+// (round to nearest, the same results as two scalar operations).
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  float2 d;
+  asm("{\n.reg .b64 ra, rb, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\n"
+      "add.rn.f32x2 rd, ra, rb;\nmov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n.reg .b64 ra, rb, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\n"
+      "sub.rn.f32x2 rd, ra, rb;\nmov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
+// Two-lane products and fused multiply-adds (round to nearest, as fmaf).
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n.reg .b64 ra, rb, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\n"
+      "mul.rn.f32x2 rd, ra, rb;\nmov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n.reg .b64 ra, rb, rc, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\n"
+      "mov.b64 rc, {%6, %7};\nfma.rn.f32x2 rd, ra, rb, rc;\nmov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
 __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
-  const float2 s02 = make_float2(a0.x + a2.x, a0.y + a2.y);
-  const float2 d02 = make_float2(a0.x - a2.x, a0.y - a2.y);
-  const float2 s13 = make_float2(a1.x + a3.x, a1.y + a3.y);
-  const float2 d13 = make_float2(a1.x - a3.x, a1.y - a3.y);
-  a0 = make_float2(s02.x + s13.x, s02.y + s13.y);
+  const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  const float2 s13 = cadd(a1, a3), d13 = csub(a1, a3);
+  a0 = cadd(s02, s13);
   a1 = make_float2(d02.x + d13.y, d02.y - d13.x);  // a0 - i a1 - a2 + i a3
-  a2 = make_float2(s02.x - s13.x, s02.y - s13.y);
+  a2 = csub(s02, s13);
   a3 = make_float2(d02.x - d13.y, d02.y + d13.x);  // a0 + i a1 - a2 - i a3
 }
 
@@ -210,15 +245,21 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
       // k0 + s0 + sg is tap j = sg - u of spectrum k0 + s0 + u, and the taps
       // of a spectrum are summed in the order j = 0, 1, 2, 3.
       {
-        float h[kTaps][8];
+        // the thread's 8 coefficients of each tap and its 8 samples of a
+        // segment as 4 pairs, so that each filter step is 4 two-lane
+        // fused multiply-adds
+        float2 h[kTaps][4];
 #pragma unroll
         for (int j = 0; j < kTaps; ++j) {
           const float4 h0 = __ldg(reinterpret_cast<const float4 *>(proto + j * kP + 4 * tid));
           const float4 h1 = __ldg(reinterpret_cast<const float4 *>(proto + j * kP + kHalf + 4 * tid));
-          h[j][0] = h0.x; h[j][1] = h0.y; h[j][2] = h0.z; h[j][3] = h0.w;
-          h[j][4] = h1.x; h[j][5] = h1.y; h[j][6] = h1.z; h[j][7] = h1.w;
+          h[j][0] = make_float2(h0.x, h0.y);
+          h[j][1] = make_float2(h0.z, h0.w);
+          h[j][2] = make_float2(h1.x, h1.y);
+          h[j][3] = make_float2(h1.z, h1.w);
         }
-        float v[kBatch][8];
+        const float2 bias = make_float2(8388736.0f, 8388736.0f);
+        float2 v[kBatch][4];
 #pragma unroll
         for (int sg = 0; sg < kBatch + kTaps - 1; ++sg) {
           const int8_t *seg = &ring[((k0 + s0 + sg) & (kRing - 1)) * kP];
@@ -228,17 +269,20 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
           const uint32_t wd[2] = {*reinterpret_cast<const uint32_t *>(seg + 4 * tid) ^ 0x80808080u,
                                   *reinterpret_cast<const uint32_t *>(seg + kHalf + 4 * tid) ^
                                       0x80808080u};
-          float xs[8];
+          float2 xs[4];
 #pragma unroll
-          for (int e = 0; e < 8; ++e)
-            xs[e] = __uint_as_float(__byte_perm(wd[e >> 2], 0x4B000000u, 0x7650 + (e & 3))) -
-                    8388736.0f;
+          for (int e = 0; e < 4; ++e)
+            xs[e] = csub(make_float2(__uint_as_float(__byte_perm(wd[e >> 1], 0x4B000000u,
+                                                                 0x7650 + 2 * (e & 1))),
+                                     __uint_as_float(__byte_perm(wd[e >> 1], 0x4B000000u,
+                                                                 0x7650 + 2 * (e & 1) + 1))),
+                         bias);
 #pragma unroll
           for (int u = 0; u < kBatch; ++u) {
             const int j = sg - u;
             if (j < 0 || j >= kTaps) continue;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[u][e] = j == 0 ? h[0][e] * xs[e] : fmaf(h[j][e], xs[e], v[u][e]);
+            for (int e = 0; e < 4; ++e) v[u][e] = j == 0 ? mul2(h[0][e], xs[e]) : fma2(h[j][e], xs[e], v[u][e]);
           }
         }
         // z[2 tid], z[2 tid + 1] and z[512 + 2 tid], z[513 + 2 tid]
@@ -247,8 +291,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 #pragma unroll
           for (int hh = 0; hh < 2; ++hh) {
             float2 *d = &buf[u * kBufElems + bpos(512 * hh + 2 * tid)];
-            d[0] = make_float2(v[u][4 * hh], v[u][4 * hh + 1]);
-            d[1] = make_float2(v[u][4 * hh + 2], v[u][4 * hh + 3]);
+            d[0] = v[u][2 * hh];
+            d[1] = v[u][2 * hh + 1];
           }
       }
       __syncthreads();
