@@ -136,6 +136,9 @@ run(64, 2, 2, 4096, 2)          # TMEM-operand kernel, 128 inputs
 run(16, 2, 5, 2048, 3)          # two-channel units, 32 inputs
 run(21, 1, 3, 1000, 2)          # ragged inputs and samples, pitched staging
 run(96, 2, 2, 4096, 1, tcn=True)  # F-engine-order staging
+os.environ["CORR_CMAC_KERNEL"] = "pair"
+run(150, 2, 2, 1024, 2)         # CTA pairs, 300 inputs
+del os.environ["CORR_CMAC_KERNEL"]
 for side in (0, 1):
     with corr.Correlator(8, 2, 2, 256) as xc:
         xc.check()

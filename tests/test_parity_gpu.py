@@ -495,3 +495,31 @@ def test_cta_pair_kernel_matches_oracle(corr, torch_cuda, oracle_mod, synth_mod,
     ov, ost = _oracle(oracle_mod, blocks, n_ant, n_pol)
     assert np.array_equal(vis, ov)
     assert np.array_equal(st, ost)
+
+
+def test_cta_pair_wait_timeout_is_reported_and_the_context_recovers(corr, torch_cuda, oracle_mod,
+                                                                    synth_mod, monkeypatch):
+    # The same self-test on the CTA-pair kernel: both CTAs of every cluster
+    # give up their waits, meet at the cluster barrier and release TMEM; the
+    # context then integrates exactly.
+    import time
+    monkeypatch.setenv("CORR_CMAC_KERNEL", "pair")
+    torch = torch_cuda
+    x0 = synth_mod.make_block(300, 4, 1024, seed=92, tones=synth_mod.random_phase_tone(300, 92))
+    x1 = synth_mod.make_block(300, 4, 1024, seed=93, tones=synth_mod.random_phase_tone(300, 93))
+    with corr.Correlator(150, 2, 4, 1024) as xc:
+        d0, d1 = torch.from_numpy(x0).cuda(), torch.from_numpy(x1).cuda()
+        xc.push_block(d0)
+        xc.check()
+        t0 = time.time()
+        xc.selftest_timeout(d1, timeout_ms=200)
+        with pytest.raises(corr.CorrError) as err:
+            xc.check()
+        assert err.value.code == corr.CORR_ETIMEOUT
+        assert 0.15 < time.time() - t0 < 10.0
+        xc.check()
+        assert xc.samples_integrated() == 1024
+        xc.push_block(d1)
+        vis, _ = xc.dump()
+        xc.check()
+    assert np.array_equal(vis.cpu().numpy(), oracle_mod.xcorr(x0) + oracle_mod.xcorr(x1))
