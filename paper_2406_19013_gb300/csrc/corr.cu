@@ -104,16 +104,15 @@ int free_ctx(corr_ctx *ctx) {
   return CORR_OK;
 }
 
-// Which CMAC kernel a context of n_in inputs runs: the TMEM-operand kernel
-// (xengine_tm.cu) for two row tiles (65..128 inputs), where it was measured
-// 5 % faster than the all-shared-memory kernel (xengine.cu), which runs
-// everything else (at 192 inputs it was 9 % faster than the TMEM-operand
-// one).  CORR_CMAC_KERNEL=tm or =smem overrides the choice.
+// Whether the TMEM-operand kernel (xengine_tm.cu) runs a context of n_in
+// inputs: only when CORR_CMAC_KERNEL=tm asks for it (up to three row tiles).
+// The all-shared-memory kernel (xengine.cu) with two-channel units measured
+// 1.25x faster at 80..128 inputs and the TMEM-operand kernel 9 % slower at
+// 192 inputs.
 bool use_tm_kernel(int n_in) {
+  (void)n_in;
   const char *e = std::getenv("CORR_CMAC_KERNEL");
-  if (e && std::strcmp(e, "tm") == 0) return true;
-  if (e && (std::strcmp(e, "smem") == 0 || std::strcmp(e, "pair") == 0)) return false;
-  return n_in > xe::kTileInputs && n_in <= 2 * xe::kTileInputs;
+  return e && std::strcmp(e, "tm") == 0;
 }
 
 // Whether CTA pairs run a context of n_in inputs (more than 256 only).  The

@@ -57,20 +57,23 @@ std::vector<XUnit> build_schedule(int N, int cover) {
   std::vector<XUnit> units;
   const int n16 = round_up(N, 16);
   const int n_rt = (N + kTileInputs - 1) / kTileInputs;
-  if (N <= kTileInputs && cover == kCoverWindow) {
-    // one row tile: a unit covers two channels (two staged regions, two
-    // accumulators), so every chunk handed from the unpack to the MMA
-    // issuers carries twice the work
+  if (N <= 2 * kTileInputs && cover == kCoverWindow) {
+    // one or two row tiles: a unit covers two channels (two staged regions,
+    // one accumulator per row tile and channel, at most 2 x 192 TMEM
+    // columns), so every chunk handed from the unpack to the MMA issuers
+    // carries twice the work
     XUnit u = empty_unit();
     u.n_chan = 2;
     for (int r = 0; r < 2; ++r) {
-      add_reg(u, 0, kTileInputs, 1);
+      add_reg(u, 0, kTileInputs * n_rt, 1);
       u.reg[r].chan_off = r;
     }
-    for (int r = 0; r < 2; ++r) {
-      add_seg(u, u.reg[r].z_row, u.reg[r].z_row, 2048, n16, 0, 0);
-      u.seg[r].chan_off = r;
-    }
+    for (int r = 0; r < 2; ++r)
+      for (int t = 0; t < n_rt; ++t) {
+        add_seg(u, u.reg[r].z_row + 128 * t, u.reg[r].z_row, 2048,
+                std::min(kTileInputs * (t + 1), n16), kTileInputs * t, 0);
+        u.seg[u.n_seg - 1].chan_off = r;
+      }
     units.push_back(u);
   } else if (N <= 256 && cover == kCoverWindow) {
     std::vector<int> tiles(n_rt);
