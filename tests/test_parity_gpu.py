@@ -384,6 +384,8 @@ def test_corner_turn_matches_oracle(corr, torch_cuda, oracle_mod, T, C, N):
 @pytest.mark.parametrize("n_ant,n_pol,C,T,fused", [
     (8, 2, 16, 1024, True),    # 16 inputs, one row tile
     (32, 2, 4, 4096, True),    # 64 inputs
+    (48, 2, 5, 1000, True),    # 96 inputs: two-channel units of two row tiles, last channel alone
+    (64, 2, 4, 2048, True),    # 128 inputs: two-channel units of two row tiles
     (96, 2, 5, 2048, True),    # the paper's 192 inputs: three row tiles
     (96, 2, 3, 1000, True),    # ragged block length
     (128, 2, 3, 1000, True),   # 256 inputs: two window units
