@@ -49,7 +49,10 @@ constexpr int kMaxBlocksPerLaunch = 8;
 struct XRegion {
   int in_lo;        // first input
   int n_in;         // inputs staged (multiple of 64; rows past N read as zero)
-  int interleaved;  // 1: A and Q rows, 0: A rows only
+  // 1: A and Q rows; 2: the interleaved layout with only the A rows written
+  // (inputs that are only columns of the unit, next to interleaved rows, so
+  // that one B operand spans both); 0: A rows only, packed (plain)
+  int interleaved;
   int z_row;        // first row in the Z stage buffer (multiple of 8)
   int pk_off;       // byte offset in the packed stage buffer
   int chan_off;     // channel: the item's first channel + chan_off

@@ -76,30 +76,29 @@ std::vector<XUnit> build_schedule(int N, int cover) {
       }
     units.push_back(u);
   } else if (N <= 256 && cover == kCoverWindow) {
-    std::vector<int> tiles(n_rt);
-    for (int t = 0; t < n_rt; ++t) tiles[t] = n_rt - 1 - t;  // largest strip first
+    // units of consecutive row tiles, largest strip first, each as many as
+    // fit 512 TMEM columns: a unit's lowest tile then bounds the inputs that
+    // are only its columns, and those need no Q rows
     std::vector<std::vector<int>> bins;
-    std::vector<int> used;
-    for (int t : tiles) {
+    int used = kTmemCols + 1;
+    for (int t = n_rt - 1; t >= 0; --t) {
       const int n = std::min(kTileInputs * (t + 1), n16);
-      bool placed = false;
-      for (size_t k = 0; k < bins.size(); ++k)
-        if (used[k] + n <= kTmemCols) {
-          bins[k].push_back(t);
-          used[k] += n;
-          placed = true;
-          break;
-        }
-      if (!placed) {
-        bins.push_back({t});
-        used.push_back(n);
+      if (used + n > kTmemCols) {
+        bins.push_back({});
+        used = 0;
       }
+      bins.back().push_back(t);
+      used += n;
     }
     for (auto &bin : bins) {
       XUnit u = empty_unit();
-      int t_max = 0;
-      for (int t : bin) t_max = std::max(t_max, t);
-      add_reg(u, 0, kTileInputs * (t_max + 1), 1);
+      int t_max = 0, t_min = n_rt;
+      for (int t : bin) t_max = std::max(t_max, t), t_min = std::min(t_min, t);
+      // inputs below the unit's lowest row tile are only its columns: their
+      // Q rows are neither decoded nor stored (same layout, so the B operand
+      // still spans the window with one stride)
+      if (t_min > 0) add_reg(u, 0, kTileInputs * t_min, 2);
+      add_reg(u, kTileInputs * t_min, kTileInputs * (t_max + 1 - t_min), 1);
       for (int t : bin)
         add_seg(u, 128 * t, 0, 2048, std::min(kTileInputs * (t + 1), n16), kTileInputs * t, 0);
       units.push_back(u);

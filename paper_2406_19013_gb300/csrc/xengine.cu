@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int r = 0; r < 2; ++r) {
         const XRegion rg = u->reg[r < n_reg ? r : 0];
         const int rr = r == 1 ? row0 - pack : row0;  // this thread's row of the region
-        il[r] = rg.interleaved;
+        il[r] = rg.interleaved == 1;  // Q rows are decoded and stored
         const int rho0 = rg.interleaved ? (((rr >> 3) << 4) | sw) : rr;
         src_off[r] = (uint32_t)(rg.pk_off + rr * kPackedRowBytes);
         dst_off[r] = (uint32_t)(rg.z_row + rho0) * 128u;
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   const int zrow = rg.z_row + (rg.interleaved ? 16 * grp : 8 * grp) + pos;
                   const uint32_t d = z_s + (uint32_t)zrow * 128u + (uint32_t)((j ^ pos) << 4);
                   sts128(d, al.x, al.y, ah.x, ah.y);
-                  if (rg.interleaved) sts128_q(d, ql.x, ql.y, qh.x, qh.y);
+                  if (rg.interleaved == 1) sts128_q(d, ql.x, ql.y, qh.x, qh.y);
                 }
               }
             }
