@@ -150,7 +150,9 @@ std::vector<XUnit> build_schedule(int N, int cover) {
         } else {
           const int lo = 256 * k;
           const int hi = row_lo + (two ? 128 : 64);
-          add_reg(u, lo, hi - lo, 1);
+          // inputs lo .. row_lo - 1 are only columns here: no Q rows
+          if (row_lo > lo) add_reg(u, lo, row_lo - lo, 2);
+          add_reg(u, row_lo, hi - row_lo, 1);
           const int a0 = 2 * (row_lo - lo);
           add_seg(u, a0, 0, 2048, std::min(row_lo + 64, n16) - lo, row_lo, lo);
           if (two) add_seg(u, a0 + 128, 0, 2048, std::min(row_lo + 128, n16) - lo, row_lo + 64, lo);
