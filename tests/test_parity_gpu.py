@@ -351,8 +351,12 @@ def test_paper_scale_sampled(corr, torch_cuda, oracle_mod, synth_mod):
     assert not vis[:, diag, 1].any()
 
 
-def test_large_n_sampled(corr, torch_cuda, oracle_mod, synth_mod):
-    # 1024 dual-pol antennas (2048 inputs), 2 channels of 4096 samples
+@pytest.mark.parametrize("kernel", ["default", "pair"])
+def test_large_n_sampled(corr, torch_cuda, oracle_mod, synth_mod, monkeypatch, kernel):
+    # 1024 dual-pol antennas (2048 inputs), 2 channels of 4096 samples, on
+    # one-CTA units (the default) and on CTA pairs
+    if kernel != "default":
+        monkeypatch.setenv("CORR_CMAC_KERNEL", kernel)
     torch = torch_cuda
     w = synth_mod.workload("large_n")
     x = w.block(0, c0=0, n_chan=2)
