@@ -36,6 +36,12 @@
 // hold several independent problems (a batch of correlators).  All waits are
 // bounded by a timeout; on expiry the kernel drains its own copies and MMAs,
 // frees TMEM and reports through *status.
+// The CTA-pair instance (PAIR) runs clusters of two CTAs on two SMs: each
+// stages and unpacks 128 rows and half of a 256-column B operand, the even
+// CTA's two issuers run M = 256 MMAs (cta_group::2) over both halves and
+// commit to both CTAs' barriers, one thread of the odd CTA forwards its
+// unpack warps' stage arrivals to the even CTA, and each CTA folds its own
+// 128 TMEM lanes.
 #include <cuda.h>
 
 #include <cstring>
