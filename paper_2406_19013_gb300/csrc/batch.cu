@@ -120,7 +120,7 @@ float time_cover(const std::vector<xe::XUnit> &units, int n_in, int C, int T, in
       cudaMemcpy(d_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice) !=
           cudaSuccess)
     goto done;
-  if (!xe::encode_block_map(d_x, T, n_in, C, T, maps.m[0])) goto done;
+  if (!xe::encode_block_map(d_x, T, n_in, C, T, maps.m[0], xe::tile_ch_rows(units))) goto done;
   p.probs = d_prob;
   p.items = d_items;
   p.cta_first = d_first;
@@ -477,7 +477,8 @@ int corr_batch_push(corr_batch *b, const uint8_t *const *d_blocks, void *stream)
         b->launches++;
         src = in.d_pitched;
       }
-      if (!xe::encode_block_map(src, in.block_len, in.n_in, in.n_chan, in.pitch, maps.m[s]))
+      if (!xe::encode_block_map(src, in.block_len, in.n_in, in.n_chan, in.pitch, maps.m[s],
+                                xe::tile_ch_rows(g.units[s])))
         return CORR_ECUDA;
     }
     xe::XParams p;

@@ -43,6 +43,7 @@ struct corr_ctx {
   uint32_t z_stage_bytes, pk_stage_bytes;
   int tm;  // 1: the TMEM-operand kernel (xengine_tm.cu) runs this context's launches
   int pair;  // 1: CTA pairs (the quad cover, M = 256 MMAs) run this context's launches
+  int ch_rows;  // inputs per channel in the TMA box (64, or 16 / 32 for multi-channel tiles)
   int pitch;           // row pitch of the staged block (block_len rounded up to 16)
   uint8_t *d_pitched;  // [n_chan][n_in][pitch] when block_len % 16 != 0
   uint8_t *d_turned;   // [n_chan][n_in][pitch]: corner-turned blocks (allocated on first use)
@@ -75,7 +76,8 @@ int cuda_err(cudaError_t e) {
 }
 
 int encode_block_map(const corr_ctx *ctx, const void *base, CUtensorMap *m) {
-  return xe::encode_block_map(base, ctx->block_len, ctx->n_in, ctx->n_chan, ctx->pitch, m)
+  return xe::encode_block_map(base, ctx->block_len, ctx->n_in, ctx->n_chan, ctx->pitch, m,
+                              ctx->ch_rows)
              ? CORR_OK
              : CORR_ECUDA;
 }
@@ -254,6 +256,7 @@ int corr_create(int n_ant, int n_pol, int n_chan, int block_len, corr_ctx **out)
     ctx->smem_bytes = TL.smem_bytes;
   }
   const std::vector<XUnit> &plan_units = ctx->tm ? tm_units : units;
+  ctx->ch_rows = ctx->tm ? xe::kTileInputs : xe::tile_ch_rows(units);
   // a fold must come before 2^24 / 128 samples have been accumulated in
   // fp32: launches of several blocks stay within that window, and the item
   // split cuts a longer block into pieces that each fold on their own
@@ -464,7 +467,7 @@ int corr_push_block_tcn(corr_ctx *ctx, const uint8_t *d_src, void *stream) {
   // The shared-memory kernel stages F-engine-order blocks directly (TMA boxes
   // of [128 samples][64 inputs], transposed on chip) when the block's strides
   // allow a tensor map; otherwise the block is turned in HBM first.
-  if (!ctx->tm && !ctx->pair && ctx->n_in % 16 == 0 &&
+  if (!ctx->tm && !ctx->pair && ctx->ch_rows == xe::kTileInputs && ctx->n_in % 16 == 0 &&
       (reinterpret_cast<uintptr_t>(d_src) & 15u) == 0)
     return launch_staged(ctx, &d_src, 1, st, 0, true);
   int rc;
@@ -643,16 +646,20 @@ int corr_plan_cover(int n_in, int cover_kind, uint8_t *cover, int *n_units,
       for (int sg = 0; sg < u.n_seg; ++sg) {
         const XSeg &s = u.seg[sg];
         if (s.chan_off != 0) continue;
-        issued += 64LL * s.n;  // 128 accumulator rows = 64 inputs x (re, im)
+        // a multi-channel tile issues its MMAs for all its channels: count
+        // the first channel's share, and only its diagonal block
+        const int cpt = s.ch_rows ? xe::kTileInputs / s.ch_rows : 1;
+        issued += 64LL * s.n / cpt;  // 128 accumulator rows = 64 inputs x (re, im)
         if (!cover) continue;
         // the epilogue's mapping: lane rho holds input row_in0 + 8 (rho / 16) + rho % 8,
         // real part when (rho / 8) is even; column n holds input col_in0 + n
         for (int rho = 0; rho < 128; ++rho) {
           if ((rho >> 3) & 1) continue;
           const int i = s.row_in0 + rank * u.pair_rows + 8 * (rho >> 4) + (rho & 7);
-          if (i >= n_in) continue;
+          if (i >= n_in || (s.ch_rows && i >= s.ch_rows)) continue;
           for (int n = 0; n < s.n; ++n) {
             const int j = s.col_in0 + n;
+            if (s.ch_rows && j >= s.ch_rows) continue;
             if (j <= i) cover[(size_t)i * n_in + j]++;
           }
         }

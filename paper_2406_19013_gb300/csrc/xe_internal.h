@@ -68,6 +68,11 @@ struct XSeg {
   int row_in0;   // input index of the tile's first row
   int col_in0;   // input index of the first column
   int chan_off;  // channel: the item's first channel + chan_off
+  // 0: the tile's rows and columns are inputs of one channel.  Otherwise the
+  // 64-row tile holds 64 / ch_rows channels of ch_rows inputs each (row and
+  // column r: channel chan_off + r / ch_rows, input r % ch_rows); only the
+  // diagonal blocks are folded
+  int ch_rows;
 };
 
 struct XUnit {

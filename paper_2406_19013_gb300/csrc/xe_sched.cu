@@ -57,7 +57,25 @@ std::vector<XUnit> build_schedule(int N, int cover) {
   std::vector<XUnit> units;
   const int n16 = round_up(N, 16);
   const int n_rt = (N + kTileInputs - 1) / kTileInputs;
-  if (N <= 2 * kTileInputs && cover == kCoverWindow) {
+  if (N <= 32 && cover == kCoverWindow) {
+    // 16 or 32 inputs at most: a 64-row tile holds 64 / n16 channels (the
+    // TMA box brings that many channels' rows at once), and a unit two such
+    // tiles; each tile's MMA also computes the cross-channel blocks, which
+    // the epilogue skips
+    XUnit u = empty_unit();
+    const int cpt = kTileInputs / n16;
+    u.n_chan = 2 * cpt;
+    for (int r = 0; r < 2; ++r) {
+      add_reg(u, 0, kTileInputs, 1);
+      u.reg[r].chan_off = r * cpt;
+    }
+    for (int r = 0; r < 2; ++r) {
+      add_seg(u, u.reg[r].z_row, u.reg[r].z_row, 2048, kTileInputs, 0, 0);
+      u.seg[r].chan_off = r * cpt;
+      u.seg[r].ch_rows = n16;
+    }
+    units.push_back(u);
+  } else if (N <= 2 * kTileInputs && cover == kCoverWindow) {
     // one or two row tiles: a unit covers two channels (two staged regions,
     // one accumulator per row tile and channel, at most 2 x 192 TMEM
     // columns), so every chunk handed from the unpack to the MMA issuers
@@ -169,6 +187,13 @@ std::vector<XUnit> build_schedule(int N, int cover) {
     for (int r = 0; r < u.n_reg; ++r)
       if (u.reg[r].n_in > kMaxRegionInputs) return {};
   return units;
+}
+
+int tile_ch_rows(const std::vector<XUnit> &units) {
+  for (const XUnit &u : units)
+    for (int s = 0; s < u.n_seg; ++s)
+      if (u.seg[s].ch_rows) return u.seg[s].ch_rows;
+  return kTileInputs;
 }
 
 bool stage_layout(const std::vector<const std::vector<XUnit> *> &unit_sets, int smem_optin,
@@ -359,13 +384,16 @@ EncodeTiledFn get_encode_fn() {
 
 }  // namespace
 
-bool encode_block_map(const void *base, int block_len, int n_in, int n_chan, int pitch, void *map) {
+bool encode_block_map(const void *base, int block_len, int n_in, int n_chan, int pitch, void *map,
+                      int ch_rows) {
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
   EncodeTiledFn enc = get_encode_fn();
   if (!enc) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)block_len, (cuuint64_t)n_in, (cuuint64_t)n_chan};
   const cuuint64_t strides[2] = {(cuuint64_t)pitch, (cuuint64_t)pitch * (cuuint64_t)n_in};
-  const cuuint32_t box[3] = {(cuuint32_t)kPkSamples, (cuuint32_t)kTileInputs, 1};
+  if (ch_rows != 16 && ch_rows != 32 && ch_rows != kTileInputs) return false;
+  const cuuint32_t box[3] = {(cuuint32_t)kPkSamples, (cuuint32_t)ch_rows,
+                             (cuuint32_t)(kTileInputs / ch_rows)};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_UINT8, 3,
                    const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

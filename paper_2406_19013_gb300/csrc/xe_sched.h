@@ -67,10 +67,17 @@ int build_items(const std::vector<ProbWork> &probs, int grid, std::vector<XItem>
                 int max_item_pk = kMaxFoldStages);
 
 // The TMA descriptor of one block, uint8 [n_chan][n_in][row pitch], 3-D
-// (time, input, channel) with 128-sample x 64-input boxes, 128B-swizzled.
-// `map` receives 128 bytes.  Returns false if the driver's encoder is
-// unavailable or rejects the arguments.
-bool encode_block_map(const void *base, int block_len, int n_in, int n_chan, int pitch, void *map);
+// (time, input, channel) with boxes of 128 samples x ch_rows inputs x
+// 64 / ch_rows channels (64 rows in all), 128B-swizzled.  ch_rows is 64
+// except for schedules whose tiles hold several channels (16 or 32, see
+// XSeg::ch_rows and tile_ch_rows).  `map` receives 128 bytes.  Returns false
+// if the driver's encoder is unavailable or rejects the arguments.
+bool encode_block_map(const void *base, int block_len, int n_in, int n_chan, int pitch, void *map,
+                      int ch_rows = kTileInputs);
+
+// Inputs per channel in a 64-row tile of a schedule's units: 16 or 32 when
+// its tiles hold several channels, else 64.
+int tile_ch_rows(const std::vector<XUnit> &units);
 
 // The TMA descriptor of one block in F-engine order, uint8 [block_len][n_chan]
 // [n_in], 3-D (input, channel, time) with 64-input x 1-channel x 128-sample

@@ -493,9 +493,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int l_in = TCN ? ((l - (g & 3)) & 7) : l;
       for (int sg = 0; sg < n_seg; ++sg) {
         const XSeg sgm = u->seg[sg];
-        const int c = item.chan + sgm.chan_off;
-        if (c >= pb.n_chan) continue;  // a two-channel unit's missing last channel
-        const int i = sgm.row_in0 + rank_rows + 8 * g + l_in;
+        // a tile of several channels: this lane's row belongs to channel
+        // block ci (the same for every lane of the warp, whose 16 rows lie in
+        // one block of at least 16)
+        const int rpc = sgm.ch_rows;
+        const int il = sgm.row_in0 + rank_rows + 8 * g + l_in;
+        const int ci = rpc ? il / rpc : 0;
+        const int c = item.chan + sgm.chan_off + ci;
+        if (c >= pb.n_chan) continue;  // a multi-channel unit's missing last channels
+        const int i = il - ci * rpc;
         const bool row_ok = i < pb.n_in;
         int64_t *arow = pb.acc + ((long long)c * pb.n_pairs + (long long)i * (i + 1) / 2) * 2;
         const long long acc_elems = (long long)pb.n_chan * pb.n_pairs * 2;
@@ -514,19 +520,24 @@ __global__ void __launch_bounds__(kThreads, 1)
             re[e] = is_im ? other : mine;
             im[e] = is_im ? mine : other;
           }
-          const int j0 = sgm.col_in0 + cb + (is_im ? 8 : 0);
+          int j0 = sgm.col_in0 + cb + (is_im ? 8 : 0);
+          bool blk_ok = true;  // the 8 columns lie in this row's channel block
+          if (rpc) {
+            blk_ok = j0 / rpc == ci;
+            j0 -= (j0 / rpc) * rpc;
+          }
           if (TCN) {
             const int rot = ((cb + (is_im ? 8 : 0)) >> 3) & 3;
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               const int jj = j0 + ((e - rot) & 7);
-              if (row_ok && jj <= i) {
+              if (row_ok && blk_ok && jj <= i) {
                 acc_add(pb.acc, acc_elems, p.status, arow + 2 * (long long)jj, re[e]);
                 acc_add(pb.acc, acc_elems, p.status, arow + 2 * (long long)jj + 1, im[e]);
               }
             }
           } else {
-            const int nvalid = row_ok ? min(8, i - j0 + 1) : 0;
+            const int nvalid = row_ok && blk_ok ? min(8, i - j0 + 1) : 0;
             int64_t *ptr = arow + 2 * (long long)j0;
 #pragma unroll
             for (int e = 0; e < 8; ++e)

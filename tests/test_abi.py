@@ -100,6 +100,14 @@ def test_every_cover_covers_lower_triangle_once(corr, n, cover):
     assert issued >= n * (n + 1) // 2
 
 
+def _chans_per_unit(n_in):
+    """Channels one window-cover unit holds: two 64-row tiles of 64 / n16
+    channels each up to 32 inputs, two channels up to two row tiles."""
+    if n_in <= 32:
+        return 2 * (64 // (-(-n_in // 16) * 16))
+    return 2 if n_in <= 128 else 1
+
+
 def _check_split(corr, n_in, n_chan, block_len, n_blocks, grid, cover=0, min_split=16):
     items, first = corr.plan_items(n_in, n_chan, block_len, n_blocks, grid, cover)
     n_tpl = corr.plan_cover(n_in, cover)[0]
@@ -111,7 +119,7 @@ def _check_split(corr, n_in, n_chan, block_len, n_blocks, grid, cover=0, min_spl
     assert np.all(np.diff(first) >= 1)  # no empty CTA
     # every (template, channel, stage) exactly once; with a single row tile
     # the window cover's unit holds two channels (the item names the first)
-    per_unit = 2 if (n_in <= 128 and cover == 0) else 1
+    per_unit = _chans_per_unit(n_in) if cover == 0 else 1
     seen = np.zeros((n_tpl, n_chan, npk), dtype=np.int32)
     for prob, tpl, chan, pk0, n in items:
         assert prob == 0 and n >= 1 and 0 <= pk0 and pk0 + n <= npk
@@ -138,7 +146,7 @@ def test_items_stay_inside_the_fold_window(corr, n_in, n_chan, block_len, n_bloc
     assert items[:, 4].max() <= corr.CORR_FOLD_SAMPLES // 128
     npk = -(-block_len // 128) * n_blocks
     n_tpl = corr.plan_cover(n_in, 0)[0]
-    per_unit = 2 if n_in <= 128 else 1  # channels per window unit
+    per_unit = _chans_per_unit(n_in)  # channels per window unit
     assert len(items) >= n_tpl * -(-n_chan // per_unit) * -(-npk // 1023)
 
 

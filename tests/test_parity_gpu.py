@@ -68,6 +68,10 @@ def test_tiny_workload(corr, torch_cuda, oracle_mod, synth_mod):
     (150, 2, 3, 512, 1),     # N = 300: row-tile pairs against 256-column pieces
     (320, 2, 2, 256, 1),     # N = 640: off-diagonal pieces
     (17, 2, 9, 2056, 1),     # N = 34, T % 32 = 8
+    (5, 2, 11, 1024, 2),     # N = 10: tiles of four 16-row channels, 11 channels (last unit partial)
+    (10, 2, 9, 2048, 1),     # N = 20: tiles of two 32-row channels, ragged rows
+    (16, 2, 3, 256, 1),      # N = 32: tiles of two full 32-row channels, 3 channels
+    (8, 1, 17, 512, 2),      # N = 8 single-pol, 17 channels
 ])
 def test_ragged_shapes(corr, torch_cuda, oracle_mod, synth_mod, n_ant, n_pol, C, T, nb):
     N = n_ant * n_pol
@@ -386,7 +390,7 @@ def test_corner_turn_matches_oracle(corr, torch_cuda, oracle_mod, T, C, N):
 
 
 @pytest.mark.parametrize("n_ant,n_pol,C,T,fused", [
-    (8, 2, 16, 1024, True),    # 16 inputs, one row tile
+    (8, 2, 16, 1024, False),   # 16 inputs: tiles of four channels -> turned in HBM
     (32, 2, 4, 4096, True),    # 64 inputs
     (48, 2, 5, 1000, True),    # 96 inputs: two-channel units of two row tiles, last channel alone
     (64, 2, 4, 2048, True),    # 128 inputs: two-channel units of two row tiles
