@@ -832,8 +832,8 @@ def run_served(args):
     rng = np.random.default_rng(11)
     n_cap = max(200, 20 * args.steps)  # requests per load level
     cap_reqs = [(0.0, int(a)) for a in rng.integers(0, len(arrays), size=n_cap)]
-    run(cap_reqs[:6], closed_q=4)  # warm-up: contexts, kernels, pinned paths
-    wall, st, total = run(cap_reqs, closed_q=4)
+    run(cap_reqs[:6], closed_q=args.served_outstanding)  # warm-up: contexts, kernels, pinned paths
+    wall, st, total = run(cap_reqs, closed_q=args.served_outstanding)
     capacity = n_cap / wall
     levels = {}
     run_per_request(cap_reqs[:6])  # warm-up
@@ -864,7 +864,7 @@ def run_served(args):
                    "l2": "blocks larger than L2"},
         "capacity": {"req_s": capacity, "tcmac_s": total / wall / 1e12,
                      "p50_ms": st["latency_p50_ms"], "p99_ms": st["latency_p99_ms"],
-                     "closed_loop_outstanding": 4},
+                     "closed_loop_outstanding": args.served_outstanding},
         "per_request_capacity": {"req_s": capacity_pr,
                                  "path": "one request at a time: corr_push_block_host + "
                                          "corr_dump_host per request, no overlap"},
@@ -978,6 +978,8 @@ def main():
                          "correlators in shared launches; corner_turn: the device reorder "
                          "of F-engine-order blocks; served: arrivals from host memory, "
                          "latency percentiles; fengine: the GPU F-engine")
+    ap.add_argument("--served-outstanding", type=int, default=4,
+                    help="served workload: requests kept outstanding while its capacity is measured")
     ap.add_argument("--fe-spectra", type=int, default=BLOCK_LEN,
                     help="fengine workload: spectra per input (profiling a smaller run)")
     ap.add_argument("--n-chan", type=int, default=N_CHAN,
