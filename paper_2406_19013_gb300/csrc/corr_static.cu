@@ -155,9 +155,9 @@ int plan_single_window(int N, xe::XUnit *units) {
       u.n_seg++;
     }
   }
-  // heaviest unit first
-  std::sort(units, units + n_bins,
-            [](const xe::XUnit &a, const xe::XUnit &b) { return a.work > b.work; });
+  // heaviest unit first (at most four: an insertion sort)
+  for (int i = 1; i < n_bins; ++i)
+    for (int j = i; j > 0 && units[j - 1].work < units[j].work; --j) std::swap(units[j - 1], units[j]);
   return n_bins;
 }
 

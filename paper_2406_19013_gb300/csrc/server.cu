@@ -101,9 +101,7 @@ class Arena {
     }
     free_[off] = bytes;
   }
-  size_t used() const { return used_; }
   size_t peak() const { return peak_; }
-  size_t free_ranges() const { return free_.size(); }
 
  private:
   size_t size_, used_ = 0, peak_ = 0;

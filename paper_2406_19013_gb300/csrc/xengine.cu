@@ -604,7 +604,7 @@ struct PairConfig {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
   PairConfig(int clusters, int smem_bytes, cudaStream_t stream) {
-    std::memset(&cfg, 0, sizeof(cfg));
+    cfg = cudaLaunchConfig_t{};
     cfg.gridDim = dim3(2 * clusters);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = (size_t)smem_bytes;
