@@ -80,6 +80,9 @@ typedef struct corr_server corr_server;
  * paper's system is n_ant = 96, n_pol = 2, n_chan = 1024 over 125 MHz,
  * Sec. 2.2).  Allocates the int64 integration buffer on the current device
  * (n_chan * P * 16 bytes, zeroed) and a few kilobytes of bookkeeping.
+ * The CMAC kernel is chosen here: the all-shared-memory kernel by default;
+ * CORR_CMAC_KERNEL=tm in the environment selects the TMEM-operand kernel
+ * (up to 192 inputs), =pair the CTA-pair kernel (more than 256 inputs).
  * On success *out owns them until corr_destroy.
  * Errors: CORR_EINVAL (non-positive size, n_pol not 1/2, block_len above
  * CORR_MAX_BLOCK_LEN, N above CORR_MAX_INPUTS, out NULL), CORR_EARCH,
@@ -273,9 +276,9 @@ int corr_corner_turn(const uint8_t *d_src, uint8_t *d_dst, int n_in, int n_chan,
  * As corr_push_block for a block in F-engine order, uint8
  * [block_len][n_chan][N] (d_src, 4-byte aligned): the Transpose step of
  * Sec. 2.1 and the correlation in one call.
- *   - When N is a multiple of 16, d_src is 16-byte aligned and the context
- *     runs the all-shared-memory CMAC kernel (the default; not with
- *     CORR_CMAC_KERNEL=tm or =pair), the CMAC kernel stages the block in this order
+ *   - When N is a multiple of 16 and above 32, d_src is 16-byte aligned and
+ *     the context runs the all-shared-memory CMAC kernel (the default; not
+ *     with CORR_CMAC_KERNEL=tm or =pair), the CMAC kernel stages the block in this order
  *     itself: its TMA boxes are [128 samples][64 inputs] of one channel and
  *     the unpack transposes them on chip.  One launch; every byte is read
  *     once.
