@@ -276,9 +276,9 @@ int corr_corner_turn(const uint8_t *d_src, uint8_t *d_dst, int n_in, int n_chan,
  * As corr_push_block for a block in F-engine order, uint8
  * [block_len][n_chan][N] (d_src, 4-byte aligned): the Transpose step of
  * Sec. 2.1 and the correlation in one call.
- *   - When N is a multiple of 16 and above 32, d_src is 16-byte aligned and
- *     the context runs the all-shared-memory CMAC kernel (the default; not
- *     with CORR_CMAC_KERNEL=tm or =pair), the CMAC kernel stages the block in this order
+ *   - When N is a multiple of 16, d_src is 16-byte aligned and the context
+ *     runs the all-shared-memory CMAC kernel (the default; not with
+ *     CORR_CMAC_KERNEL=tm or =pair), the CMAC kernel stages the block in this order
  *     itself: its TMA boxes are [128 samples][64 inputs] of one channel and
  *     the unpack transposes them on chip.  One launch; every byte is read
  *     once.

@@ -371,7 +371,8 @@ int launch_staged(corr_ctx *ctx, const uint8_t *const *staged, int nb, cudaStrea
   p.tcn = tcn ? 1 : 0;
   for (int k = 0; k < nb; ++k) {
     if (tcn) {
-      if (!xe::encode_block_map_tcn(staged[k], ctx->block_len, ctx->n_in, ctx->n_chan, maps.m[k]))
+      if (!xe::encode_block_map_tcn(staged[k], ctx->block_len, ctx->n_in, ctx->n_chan, maps.m[k],
+                                    ctx->ch_rows))
         return CORR_ECUDA;
     } else if ((rc = encode_block_map(ctx, staged[k], reinterpret_cast<CUtensorMap *>(maps.m[k]))) !=
                CORR_OK) {
@@ -467,7 +468,7 @@ int corr_push_block_tcn(corr_ctx *ctx, const uint8_t *d_src, void *stream) {
   // The shared-memory kernel stages F-engine-order blocks directly (TMA boxes
   // of [128 samples][64 inputs], transposed on chip) when the block's strides
   // allow a tensor map; otherwise the block is turned in HBM first.
-  if (!ctx->tm && !ctx->pair && ctx->ch_rows == xe::kTileInputs && ctx->n_in % 16 == 0 &&
+  if (!ctx->tm && !ctx->pair && ctx->n_in % 16 == 0 &&
       (reinterpret_cast<uintptr_t>(d_src) & 15u) == 0)
     return launch_staged(ctx, &d_src, 1, st, 0, true);
   int rc;

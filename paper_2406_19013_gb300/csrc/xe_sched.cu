@@ -402,12 +402,17 @@ bool encode_block_map(const void *base, int block_len, int n_in, int n_chan, int
   return r == CUDA_SUCCESS;
 }
 
-bool encode_block_map_tcn(const void *base, int block_len, int n_in, int n_chan, void *map) {
+bool encode_block_map_tcn(const void *base, int block_len, int n_in, int n_chan, void *map,
+                          int ch_rows) {
   EncodeTiledFn enc = get_encode_fn();
   if (!enc || n_in % 16 != 0) return false;
+  if (ch_rows != 16 && ch_rows != 32 && ch_rows != kTileInputs) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)n_in, (cuuint64_t)n_chan, (cuuint64_t)block_len};
   const cuuint64_t strides[2] = {(cuuint64_t)n_in, (cuuint64_t)n_in * (cuuint64_t)n_chan};
-  const cuuint32_t box[3] = {(cuuint32_t)kTileInputs, 1, (cuuint32_t)kPkSamples};
+  // ch_rows inputs of 64 / ch_rows channels: each sample of the box is still
+  // 64 bytes, channel-major, as the tile's rows are
+  const cuuint32_t box[3] = {(cuuint32_t)ch_rows, (cuuint32_t)(kTileInputs / ch_rows),
+                             (cuuint32_t)kPkSamples};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_UINT8, 3,
                    const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

@@ -83,6 +83,7 @@ int tile_ch_rows(const std::vector<XUnit> &units);
 // [n_in], 3-D (input, channel, time) with 64-input x 1-channel x 128-sample
 // boxes, no swizzle (each box lands as [128 samples][64 inputs]).  The
 // channel and time strides must be multiples of 16 bytes: n_in % 16 == 0.
-bool encode_block_map_tcn(const void *base, int block_len, int n_in, int n_chan, void *map);
+bool encode_block_map_tcn(const void *base, int block_len, int n_in, int n_chan, void *map,
+                          int ch_rows = kTileInputs);
 
 }  // namespace xe

@@ -390,7 +390,8 @@ def test_corner_turn_matches_oracle(corr, torch_cuda, oracle_mod, T, C, N):
 
 
 @pytest.mark.parametrize("n_ant,n_pol,C,T,fused", [
-    (8, 2, 16, 1024, False),   # 16 inputs: tiles of four channels -> turned in HBM
+    (8, 2, 16, 1024, True),    # 16 inputs: tiles of four channels, boxes of 16 inputs x 4 channels
+    (16, 2, 5, 512, True),     # 32 inputs: tiles of two channels
     (32, 2, 4, 4096, True),    # 64 inputs
     (48, 2, 5, 1000, True),    # 96 inputs: two-channel units of two row tiles, last channel alone
     (64, 2, 4, 2048, True),    # 128 inputs: two-channel units of two row tiles
