@@ -231,3 +231,16 @@ def test_debug_variant_builds_and_exports(corr):
         assert hasattr(lib, name), name
     lib.corr_debug_build.restype = ctypes.c_int
     assert lib.corr_debug_build() == 1
+
+
+@pytest.mark.parametrize("n,issuers,iters,a_tmem", [
+    (8, 1, 10, 0), (264, 1, 10, 0), (100, 1, 10, 0),   # N outside 16..256 or not a multiple of 16
+    (256, 0, 10, 0), (256, 5, 10, 0),                   # issuing threads outside 1..4
+    (256, 1, 0, 0), (256, 1, 10, 2),                    # no iterations; A source not 0/1
+    (256, 2, 10, 1),                                    # 2 x 256 + 32 TMEM columns > 512
+])
+def test_mma_rate_rejects_before_any_device_work(corr, n, issuers, iters, a_tmem):
+    status = np.zeros(1, dtype=np.int32)  # never touched: the call fails its checks first
+    rc = corr.load().corr_mma_rate(n, issuers, iters, a_tmem, status.ctypes.data, None, None)
+    assert rc == corr.CORR_EINVAL
+    assert corr.load().corr_mma_rate(256, 1, 10, 0, None, None, None) == corr.CORR_EINVAL

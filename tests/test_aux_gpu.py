@@ -167,3 +167,14 @@ def test_release_build_has_no_debug_hooks(corr, torch_cuda):
         with pytest.raises(corr.CorrError) as e:
             xc.debug_corrupt_guard(0)
         assert e.value.code == corr.CORR_ESTATE
+
+
+def test_mma_rate_measures_a_plausible_fp8_rate(corr, torch_cuda):
+    """The roofline's denominator: a short run of the dense E5M2 MMA loop
+    (N = 256, A from TMEM) finishes with a clear status and lands between
+    half and 1.2x the nominal dense fp8 rate of the part (4.5 PFLOP/s), at
+    a cycle count per MMA near 128 x 256 x 32 MACs / 8192 per clock."""
+    tflops, ms, cyc = corr.mma_rate(n=256, issuers=1, iters=2000, a_from_tmem=True, reps=2)
+    assert 2250 < tflops < 5400, tflops
+    assert 100 < cyc < 300, cyc
+    assert ms > 0
