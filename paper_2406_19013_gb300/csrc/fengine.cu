@@ -34,8 +34,9 @@
 //   - the standard split of the real FFT, folded with the EQ gain into two
 //     complex constants per channel, gives g X[c] = A_c Z[c] + B_c conj Z[N-c]
 //     (A_c = g (1 - i W_2048^c) / 2, B_c = g (1 + i W_2048^c) / 2), then
-//     requantisation; each thread packs one channel's codes of the batch's 4
-//     spectra into a word of a staging tile [1024 channels][kSpecTile spectra];
+//     requantisation; a thread takes a channel c and its mirror N - c, which
+//     read the same two FFT outputs, and packs each one's codes of the batch's
+//     4 spectra into a word of a staging tile [1024 channels][kSpecTile spectra];
 //   - each channel's row of the staging tile is written out as one 32-byte run
 //     of out[c][input][k0 ..].
 // Floating point is fp32 (the host computes the filter and twiddles in
@@ -164,7 +165,11 @@ constexpr int kRingBytes = kRing * kP;            // 32 KB
 // per 64).  That keeps the passes' runs of consecutive elements and their
 // stride-64 gathers at the two shared-memory wavefronts a warp's float2
 // access needs, and every unrolled access of a pass is its thread's base
-// plus a constant offset.
+// plus a constant offset.  The filter's output is the one exception: it is
+// stored unpadded (element e at e), so that each thread's two consecutive
+// elements leave as one aligned 16-byte store (padded, a warp's 8-byte stores
+// 16 bytes apart took four wavefronts instead of two), and the first pass
+// reads it from there; the first pass's reads all precede its padded writes.
 constexpr int kBufElems = kHalf + kHalf / 64;
 constexpr int kBufBytes = kBatch * kBufElems * 8;
 
@@ -285,15 +290,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             for (int e = 0; e < 4; ++e) v[u][e] = j == 0 ? mul2(h[0][e], xs[e]) : fma2(h[j][e], xs[e], v[u][e]);
           }
         }
-        // z[2 tid], z[2 tid + 1] and z[512 + 2 tid], z[513 + 2 tid]
+        // z[2 tid], z[2 tid + 1] and z[512 + 2 tid], z[513 + 2 tid], unpadded:
+        // one 16-byte store per pair, a warp's lanes contiguous
 #pragma unroll
         for (int u = 0; u < kBatch; ++u)
 #pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
-            float2 *d = &buf[u * kBufElems + bpos(512 * hh + 2 * tid)];
-            d[0] = v[u][2 * hh];
-            d[1] = v[u][2 * hh + 1];
-          }
+          for (int hh = 0; hh < 2; ++hh)
+            *reinterpret_cast<float4 *>(&buf[u * kBufElems + 512 * hh + 2 * tid]) =
+                make_float4(v[u][2 * hh].x, v[u][2 * hh].y, v[u][2 * hh + 1].x, v[u][2 * hh + 1].y);
       }
       __syncthreads();
       // ---- 1024-point FFTs, 1024 = 16 x 4 x 16 (n = 64 m1 + 16 m2 + n2,
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         const bool live = u < nb;
         if (live) {
 #pragma unroll
-          for (int m1 = 0; m1 < 16; ++m1) a[m1] = bu[bpos(64 * m1 + r)];
+          for (int m1 = 0; m1 < 16; ++m1) a[m1] = bu[64 * m1 + r];  // the filter's unpadded output
           dft16(a);
 #pragma unroll
           for (int l1 = 1; l1 < 16; ++l1) a[l1] = cmul(a[l1], tw64[m2 * l1]);
@@ -358,32 +362,47 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         }
       }
       __syncthreads();
-      // ---- real-FFT split with the EQ gain, requantisation: channels
-      // c = tid + 256 e.  With Z[c] = p + i q and Z[N - c] = r + i s,
+      // ---- real-FFT split with the EQ gain, requantisation.  Channel c and
+      // its mirror m = N - c read the same two FFT outputs, so one thread
+      // takes both: c = tid + 256 e (e = 0, 1) with m = N - c, except that
+      // thread 0 takes the two channels that are their own mirrors, 0 and
+      // N / 2, at e = 0.  With Z[c] = p + i q and Z[N - c] = r + i s,
       //   g X[c] = A Z[c] + B conj Z[N - c]
       //          = (A.x p - A.y q + B.x r + B.y s) + i (A.x q + A.y p + B.y r - B.x s).
 #pragma unroll 1
-      for (int e = 0; e < 4; ++e) {
+      for (int e = 0; e < 2; ++e) {
         const int c = tid + kThreads * e;
-        const float g = __ldg(eq + (long long)in * kHalf + c);  // EQ gain
-        const float2 sa = __ldg(split_a + c), sb = __ldg(split_b + c);
-        const float2 A = make_float2(g * sa.x, g * sa.y), B = make_float2(g * sb.x, g * sb.y);
-        const int cr = (kHalf - c) & (kHalf - 1);
-        uint32_t word = 0;
+        const bool self = c == 0;
+        const int m = self ? kHalf / 2 : kHalf - c;
+        const float gc = __ldg(eq + (long long)in * kHalf + c);  // EQ gains
+        const float gm = __ldg(eq + (long long)in * kHalf + m);
+        const float2 sac = __ldg(split_a + c), sbc = __ldg(split_b + c);
+        const float2 sam = __ldg(split_a + m), sbm = __ldg(split_b + m);
+        const float2 Ac = make_float2(gc * sac.x, gc * sac.y), Bc = make_float2(gc * sbc.x, gc * sbc.y);
+        const float2 Am = make_float2(gm * sam.x, gm * sam.y), Bm = make_float2(gm * sbm.x, gm * sbm.y);
+        uint32_t wc = 0, wm = 0;
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
           const float2 zc = buf[u * kBufElems + bpos(c)];
-          const float2 zr = buf[u * kBufElems + bpos(cr)];
-          const float gx = fmaf(A.x, zc.x, fmaf(-A.y, zc.y, fmaf(B.x, zr.x, B.y * zr.y)));
-          const float gy = fmaf(A.x, zc.y, fmaf(A.y, zc.x, fmaf(B.y, zr.x, -B.x * zr.y)));
+          const float2 zm = buf[u * kBufElems + bpos(m)];
+          const float2 rc = self ? zc : zm;  // Z[N - c]
+          const float2 rm = self ? zm : zc;  // Z[N - m]
+          const float gxc = fmaf(Ac.x, zc.x, fmaf(-Ac.y, zc.y, fmaf(Bc.x, rc.x, Bc.y * rc.y)));
+          const float gyc = fmaf(Ac.x, zc.y, fmaf(Ac.y, zc.x, fmaf(Bc.y, rc.x, -Bc.x * rc.y)));
+          const float gxm = fmaf(Am.x, zm.x, fmaf(-Am.y, zm.y, fmaf(Bm.x, rm.x, Bm.y * rm.y)));
+          const float gym = fmaf(Am.x, zm.y, fmaf(Am.y, zm.x, fmaf(Bm.y, rm.x, -Bm.x * rm.y)));
           if (kQuant) {
-            const int qr = quant(gx), qi = quant(gy);
-            word |= (uint32_t)(((qr & 15) << 4) | (qi & 15)) << (8 * u);
+            wc |= (uint32_t)(((quant(gxc) & 15) << 4) | (quant(gyc) & 15)) << (8 * u);
+            wm |= (uint32_t)(((quant(gxm) & 15) << 4) | (quant(gym) & 15)) << (8 * u);
           } else if (u < nb) {
-            out_spec[((long long)c * n_in + in) * n_spec + k0 + s0 + u] = make_float2(gx, gy);
+            out_spec[((long long)c * n_in + in) * n_spec + k0 + s0 + u] = make_float2(gxc, gyc);
+            out_spec[((long long)m * n_in + in) * n_spec + k0 + s0 + u] = make_float2(gxm, gym);
           }
         }
-        if (kQuant) *reinterpret_cast<uint32_t *>(&stage[c * kStagePitch + s0]) = word;
+        if (kQuant) {
+          *reinterpret_cast<uint32_t *>(&stage[c * kStagePitch + s0]) = wc;
+          *reinterpret_cast<uint32_t *>(&stage[m * kStagePitch + s0]) = wm;
+        }
       }
       __syncthreads();  // buf and the ring slots are reused by the next batch
     }
