@@ -554,7 +554,7 @@ int corr_fengine_create(int n_in, int n_spectra, corr_fengine **out);
 /* Copies EQ gains float[n_in][1024] from host memory (synchronous). */
 int corr_fengine_set_eq(corr_fengine *f, const float *h_eq);
 
-/* d_adc: int8[n_in][(n_spectra + 3) * 2048] device samples (8-byte aligned);
+/* d_adc: int8[n_in][(n_spectra + 3) * 2048] device samples (16-byte aligned);
  * d_out: uint8[1024][n_in][n_spectra] device (16-byte aligned), overwritten.
  * Stream-ordered and asynchronous.  Errors: CORR_EINVAL, CORR_ECUDA. */
 int corr_fengine_run(corr_fengine *f, const int8_t *d_adc, uint8_t *d_out, void *stream);

@@ -181,11 +181,23 @@ constexpr int kStageBytes = kHalf * kStagePitch;  // 36 KB
 
 __device__ __forceinline__ int bpos(int e) { return e + (e >> 6); }
 
-// 8-byte asynchronous copy global -> shared; src_bytes 0 writes zeros.
-__device__ __forceinline__ void cp_async8(void *dst, const void *src, int src_bytes) {
+// 16-byte asynchronous copy global -> shared, cached in L2 only, so that the
+// streamed samples do not evict the filter coefficients from L1; src_bytes 0
+// writes zeros.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(src_bytes)
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes)
                : "memory");
+}
+// A 16-byte read-only load that the compiler keeps where it is written (it
+// neither re-issues it at the use nor moves it across the barriers), so that
+// the next batch's coefficients are in flight while the current batch ends.
+__device__ __forceinline__ float4 ldg_keep(const float *p) {
+  float4 v;
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -217,14 +229,27 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
   const int n_seg = n_spec + kTaps - 1;  // segments in one input's stream
   const long long stream_len = (long long)n_seg * kP;
 
-  // starts the copy of this thread's 8 bytes of segment seg into its ring
-  // slot; segments past the stream's end read as zero (they feed only
-  // spectra past n_spec, which are computed and dropped)
-  auto fetch_seg = [&](const int8_t *x, int seg) {
+  // starts the copy of 16-byte piece p of segment seg into its ring slot;
+  // segments past the stream's end read as zero (they feed only spectra past
+  // n_spec, which are computed and dropped)
+  constexpr int kPieces = kP / 16;
+  auto fetch_piece = [&](const int8_t *x, int seg, int p) {
     const bool in = seg < n_seg;
-    cp_async8(&ring[(seg & (kRing - 1)) * kP + 8 * tid],
-              x + (in ? (long long)seg * kP + 8 * tid : 0), in ? 8 : 0);
+    cp_async16(&ring[(seg & (kRing - 1)) * kP + 16 * p],
+               x + (in ? (long long)seg * kP + 16 * p : 0), in ? 16 : 0);
   };
+  // the thread's 8 coefficients of each tap (samples 4 t .. 4 t + 3 and
+  // 1024 + 4 t .. + 3), the same for every batch; loaded here for the first
+  // batch and at the end of each batch for the next
+  float4 hq[2 * kTaps];
+  auto load_h = [&]() {
+#pragma unroll
+    for (int j = 0; j < kTaps; ++j) {
+      hq[2 * j] = ldg_keep(proto + j * kP + 4 * tid);
+      hq[2 * j + 1] = ldg_keep(proto + j * kP + kHalf + 4 * tid);
+    }
+  };
+  load_h();
 
   for (long long w = blockIdx.x; w < (long long)n_in * n_tiles; w += gridDim.x) {
     const int in = (int)(w / n_tiles), tile = (int)(w % n_tiles);
@@ -232,15 +257,16 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     const int ns = min(kSpecTile, n_spec - k0);
     const int8_t *x = adc + (long long)in * stream_len;
     // the first batch's segments k0 .. k0 + kBatch + 2
-#pragma unroll
-    for (int j = 0; j < kBatch + kTaps - 1; ++j) fetch_seg(x, k0 + j);
+    for (int i = tid; i < (kBatch + kTaps - 1) * kPieces; i += kThreads)
+      fetch_piece(x, k0 + i / kPieces, i % kPieces);
     cp_async_commit();
     for (int s0 = 0; s0 < ns; s0 += kBatch) {
       const int nb = min(kBatch, ns - s0);  // spectra of this batch that are kept
       // the next batch's newest segments, while this batch computes
       if (s0 + kBatch < ns) {
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) fetch_seg(x, k0 + s0 + kBatch + kTaps - 1 + u);
+        for (int i = tid; i < kBatch * kPieces; i += kThreads)
+          fetch_piece(x, k0 + s0 + kBatch + kTaps - 1 + i / kPieces, i % kPieces);
       }
       cp_async_commit();
       cp_async_wait<1>();  // this batch's segments have landed (this thread's part)
@@ -256,12 +282,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         float2 h[kTaps][4];
 #pragma unroll
         for (int j = 0; j < kTaps; ++j) {
-          const float4 h0 = __ldg(reinterpret_cast<const float4 *>(proto + j * kP + 4 * tid));
-          const float4 h1 = __ldg(reinterpret_cast<const float4 *>(proto + j * kP + kHalf + 4 * tid));
-          h[j][0] = make_float2(h0.x, h0.y);
-          h[j][1] = make_float2(h0.z, h0.w);
-          h[j][2] = make_float2(h1.x, h1.y);
-          h[j][3] = make_float2(h1.z, h1.w);
+          h[j][0] = make_float2(hq[2 * j].x, hq[2 * j].y);
+          h[j][1] = make_float2(hq[2 * j].z, hq[2 * j].w);
+          h[j][2] = make_float2(hq[2 * j + 1].x, hq[2 * j + 1].y);
+          h[j][3] = make_float2(hq[2 * j + 1].z, hq[2 * j + 1].w);
         }
         const float2 bias = make_float2(8388736.0f, 8388736.0f);
         float2 v[kBatch][4];
@@ -404,6 +428,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
           *reinterpret_cast<uint32_t *>(&stage[m * kStagePitch + s0]) = wm;
         }
       }
+      load_h();         // the next batch's coefficients, in flight across the barrier
       __syncthreads();  // buf and the ring slots are reused by the next batch
     }
     if (kQuant) {
@@ -533,7 +558,7 @@ int corr_fengine_set_eq(corr_fengine *f, const float *h_eq) {
 
 int corr_fengine_run(corr_fengine *f, const int8_t *d_adc, uint8_t *d_out, void *stream) {
   CORR_TRACE("corr_fengine_run");
-  if (!f || !d_adc || !d_out || !aligned(d_adc, 8) || !aligned(d_out, 16)) return CORR_EINVAL;
+  if (!f || !d_adc || !d_out || !aligned(d_adc, 16) || !aligned(d_out, 16)) return CORR_EINVAL;
   const long long work = (long long)f->n_in * ((f->n_spec + kSpecTile - 1) / kSpecTile);
   const int grid = (int)std::min<long long>(work, (long long)f->n_sm * kCtasPerSm * 4);
   fengine_kernel<1><<<grid, kThreads, smem_bytes(), static_cast<cudaStream_t>(stream)>>>(
@@ -543,7 +568,7 @@ int corr_fengine_run(corr_fengine *f, const int8_t *d_adc, uint8_t *d_out, void 
 
 int corr_fengine_spectra(corr_fengine *f, const int8_t *d_adc, float *d_spec, void *stream) {
   CORR_TRACE("corr_fengine_spectra");
-  if (!f || !d_adc || !d_spec || !aligned(d_adc, 8) || !aligned(d_spec, 8)) return CORR_EINVAL;
+  if (!f || !d_adc || !d_spec || !aligned(d_adc, 16) || !aligned(d_spec, 8)) return CORR_EINVAL;
   const long long work = (long long)f->n_in * ((f->n_spec + kSpecTile - 1) / kSpecTile);
   const int grid = (int)std::min<long long>(work, (long long)f->n_sm * kCtasPerSm * 4);
   fengine_kernel<0><<<grid, kThreads, smem_bytes(), static_cast<cudaStream_t>(stream)>>>(
