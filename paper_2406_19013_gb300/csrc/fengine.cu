@@ -31,12 +31,13 @@
 //   - a 1024-point complex FFT runs in three in-place passes over shared
 //     memory, 1024 = 16 x 4 x 16 (each thread does a 16-point FFT in registers
 //     in the first and last pass, four 4-point FFTs in the middle one);
-//   - the standard split of the real FFT, folded with the EQ gain into two
-//     complex constants per channel, gives g X[c] = A_c Z[c] + B_c conj Z[N-c]
-//     (A_c = g (1 - i W_2048^c) / 2, B_c = g (1 + i W_2048^c) / 2), then
+//   - the standard split of the real FFT, X[c] = s_c Z[c] + (1 - s_c)
+//     conj Z[N-c] with s_c = (1 - i W_2048^c) / 2, then the EQ gain and
 //     requantisation; a thread takes a channel c and its mirror N - c, which
-//     read the same two FFT outputs, and packs each one's codes of the batch's
-//     4 spectra into a word of a staging tile [1024 channels][kSpecTile spectra];
+//     read the same two FFT outputs and whose split constants are conjugate,
+//     so that one complex multiply-add gives both, and packs each one's codes
+//     of the batch's 4 spectra into a word of a staging tile
+//     [1024 channels][kSpecTile spectra];
 //   - each channel's row of the staging tile is written out as one 32-byte run
 //     of out[c][input][k0 ..].
 // Floating point is fp32 (the host computes the filter and twiddles in
@@ -212,8 +213,8 @@ static_assert(kRing >= kTaps - 1 + 2 * kBatch && (kRing & (kRing - 1)) == 0, "ri
 template <int kQuant>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     fengine_kernel(const int8_t *__restrict__ adc, const float *__restrict__ proto,
-                   const float2 *__restrict__ tw_fft, const float2 *__restrict__ split_a,
-                   const float2 *__restrict__ split_b, const float *__restrict__ eq,
+                   const float2 *__restrict__ tw_fft, const float2 *__restrict__ split,
+                   const float *__restrict__ eq,
                    uint8_t *__restrict__ out_codes, float2 *__restrict__ out_spec, int n_in,
                    int n_spec) {
   extern __shared__ __align__(16) uint8_t fe_smem[];
@@ -386,47 +387,66 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         }
       }
       __syncthreads();
-      // ---- real-FFT split with the EQ gain, requantisation.  Channel c and
-      // its mirror m = N - c read the same two FFT outputs, so one thread
-      // takes both: c = tid + 256 e (e = 0, 1) with m = N - c, except that
-      // thread 0 takes the two channels that are their own mirrors, 0 and
-      // N / 2, at e = 0.  With Z[c] = p + i q and Z[N - c] = r + i s,
-      //   g X[c] = A Z[c] + B conj Z[N - c]
-      //          = (A.x p - A.y q + B.x r + B.y s) + i (A.x q + A.y p + B.y r - B.x s).
+      // ---- real-FFT split with the EQ gain, requantisation.  With
+      // s_c = (1 - i W_2048^c) / 2 the split is X[c] = s_c Z[c] + (1 - s_c)
+      // conj Z[N - c].  Channel c and its mirror m = N - c read the same two
+      // FFT outputs P = Z[c] and R = Z[m], and since s_m = conj s_c,
+      //   X[c] = U = conj R + s_c (P - conj R),
+      //   X[m] = conj V,   V = P - s_c (P - conj R) = (P + conj R) - U,
+      // so one thread takes both: c = tid + 256 e (e = 0, 1) and m = N - c,
+      // except that thread 0 takes the self-mirrored N / 2 (as both c and m)
+      // at e = 0, and channel 0 (also its own mirror) after the loop.
+      const float2 k_mp = make_float2(-1.0f, 1.0f), k_pm = make_float2(1.0f, -1.0f);
 #pragma unroll 1
       for (int e = 0; e < 2; ++e) {
-        const int c = tid + kThreads * e;
-        const bool self = c == 0;
-        const int m = self ? kHalf / 2 : kHalf - c;
+        const int c = tid + kThreads * e == 0 ? kHalf / 2 : tid + kThreads * e;
+        const int m = kHalf - c;
         const float gc = __ldg(eq + (long long)in * kHalf + c);  // EQ gains
         const float gm = __ldg(eq + (long long)in * kHalf + m);
-        const float2 sac = __ldg(split_a + c), sbc = __ldg(split_b + c);
-        const float2 sam = __ldg(split_a + m), sbm = __ldg(split_b + m);
-        const float2 Ac = make_float2(gc * sac.x, gc * sac.y), Bc = make_float2(gc * sbc.x, gc * sbc.y);
-        const float2 Am = make_float2(gm * sam.x, gm * sam.y), Bm = make_float2(gm * sbm.x, gm * sbm.y);
+        const float2 sc = __ldg(split + c);
+        const float2 gcc = make_float2(gc, gc), gmm = make_float2(gm, -gm);
         uint32_t wc = 0, wm = 0;
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
-          const float2 zc = buf[u * kBufElems + bpos(c)];
-          const float2 zm = buf[u * kBufElems + bpos(m)];
-          const float2 rc = self ? zc : zm;  // Z[N - c]
-          const float2 rm = self ? zm : zc;  // Z[N - m]
-          const float gxc = fmaf(Ac.x, zc.x, fmaf(-Ac.y, zc.y, fmaf(Bc.x, rc.x, Bc.y * rc.y)));
-          const float gyc = fmaf(Ac.x, zc.y, fmaf(Ac.y, zc.x, fmaf(Bc.y, rc.x, -Bc.x * rc.y)));
-          const float gxm = fmaf(Am.x, zm.x, fmaf(-Am.y, zm.y, fmaf(Bm.x, rm.x, Bm.y * rm.y)));
-          const float gym = fmaf(Am.x, zm.y, fmaf(Am.y, zm.x, fmaf(Bm.y, rm.x, -Bm.x * rm.y)));
+          const float2 P = buf[u * kBufElems + bpos(c)];
+          const float2 R = buf[u * kBufElems + bpos(m)];
+          const float2 D = fma2(R, k_mp, P);  // P - conj R
+          const float2 F = fma2(R, k_pm, P);  // P + conj R
+          const float2 U = make_float2(fmaf(sc.x, D.x, fmaf(-sc.y, D.y, R.x)),
+                                       fmaf(sc.x, D.y, fmaf(sc.y, D.x, -R.y)));
+          const float2 xc = mul2(gcc, U);          // g X[c]
+          const float2 xm = mul2(gmm, csub(F, U));  // g X[m] = g conj V
           if (kQuant) {
-            wc |= (uint32_t)(((quant(gxc) & 15) << 4) | (quant(gyc) & 15)) << (8 * u);
-            wm |= (uint32_t)(((quant(gxm) & 15) << 4) | (quant(gym) & 15)) << (8 * u);
+            wc |= (uint32_t)(((quant(xc.x) & 15) << 4) | (quant(xc.y) & 15)) << (8 * u);
+            wm |= (uint32_t)(((quant(xm.x) & 15) << 4) | (quant(xm.y) & 15)) << (8 * u);
           } else if (u < nb) {
-            out_spec[((long long)c * n_in + in) * n_spec + k0 + s0 + u] = make_float2(gxc, gyc);
-            out_spec[((long long)m * n_in + in) * n_spec + k0 + s0 + u] = make_float2(gxm, gym);
+            out_spec[((long long)c * n_in + in) * n_spec + k0 + s0 + u] = xc;
+            out_spec[((long long)m * n_in + in) * n_spec + k0 + s0 + u] = xm;
           }
         }
         if (kQuant) {
           *reinterpret_cast<uint32_t *>(&stage[c * kStagePitch + s0]) = wc;
           *reinterpret_cast<uint32_t *>(&stage[m * kStagePitch + s0]) = wm;
         }
+      }
+      if (tid == 0) {
+        // channel 0: R = P = Z[0]
+        const float g0 = __ldg(eq + (long long)in * kHalf);
+        const float2 s_0 = __ldg(split);
+        uint32_t w0 = 0;
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const float2 P = buf[u * kBufElems];
+          const float2 D = fma2(P, k_mp, P);
+          const float2 x0 = make_float2(g0 * fmaf(s_0.x, D.x, fmaf(-s_0.y, D.y, P.x)),
+                                        g0 * fmaf(s_0.x, D.y, fmaf(s_0.y, D.x, -P.y)));
+          if (kQuant) {
+            w0 |= (uint32_t)(((quant(x0.x) & 15) << 4) | (quant(x0.y) & 15)) << (8 * u);
+          } else if (u < nb) {
+            out_spec[(long long)in * n_spec + k0 + s0 + u] = x0;
+          }
+        }
+        if (kQuant) *reinterpret_cast<uint32_t *>(&stage[s0]) = w0;
       }
       load_h();         // the next batch's coefficients, in flight across the barrier
       __syncthreads();  // buf and the ring slots are reused by the next batch
@@ -458,7 +478,7 @@ constexpr int smem_bytes() { return kRingBytes + kBufBytes + kStageBytes; }
 struct corr_fengine {
   int n_in, n_spec, n_sm;
   float *d_proto;
-  float2 *d_tw_fft, *d_split_a, *d_split_b;
+  float2 *d_tw_fft, *d_split;
   float *d_eq;
 };
 
@@ -474,8 +494,7 @@ void free_fengine(corr_fengine *f) {
   if (!f) return;
   cudaFree(f->d_proto);
   cudaFree(f->d_tw_fft);
-  cudaFree(f->d_split_a);
-  cudaFree(f->d_split_b);
+  cudaFree(f->d_split);
   cudaFree(f->d_eq);
   delete f;
 }
@@ -511,15 +530,14 @@ int corr_fengine_create(int n_in, int n_spectra, corr_fengine **out) {
     const double sinc = xx == 0.0 ? 1.0 : std::sin(pi * xx) / (pi * xx);
     proto[m] = (float)(w * sinc);
   }
-  // FFT twiddles W_1024^k, and the real-FFT split's constants per channel:
+  // FFT twiddles W_1024^k, and the real-FFT split's constant per channel:
   // with W = W_2048^c = cos t - i sin t (t = 2 pi c / 2048),
-  // (1 - i W) / 2 = ((1 - sin t) / 2, -cos t / 2) and (1 + i W) / 2 = ((1 + sin t) / 2, cos t / 2)
-  std::vector<float2> tw_fft(kHalf), split_a(kHalf), split_b(kHalf);
+  // s_c = (1 - i W) / 2 = ((1 - sin t) / 2, -cos t / 2)
+  std::vector<float2> tw_fft(kHalf), split(kHalf);
   for (int k = 0; k < kHalf; ++k) {
     tw_fft[k] = make_float2((float)std::cos(2.0 * pi * k / kHalf), (float)-std::sin(2.0 * pi * k / kHalf));
     const double t = 2.0 * pi * k / kP, ct = std::cos(t), st = std::sin(t);
-    split_a[k] = make_float2((float)(0.5 * (1.0 - st)), (float)(-0.5 * ct));
-    split_b[k] = make_float2((float)(0.5 * (1.0 + st)), (float)(0.5 * ct));
+    split[k] = make_float2((float)(0.5 * (1.0 - st)), (float)(-0.5 * ct));
   }
   int rc;
   if ((rc = cuda_err(cudaFuncSetAttribute(fengine_kernel<1>,
@@ -530,16 +548,13 @@ int corr_fengine_create(int n_in, int n_spectra, corr_fengine **out) {
                                           smem_bytes()))) != CORR_OK ||
       (rc = cuda_err(cudaMalloc(&f->d_proto, L * sizeof(float)))) != CORR_OK ||
       (rc = cuda_err(cudaMalloc(&f->d_tw_fft, kHalf * sizeof(float2)))) != CORR_OK ||
-      (rc = cuda_err(cudaMalloc(&f->d_split_a, kHalf * sizeof(float2)))) != CORR_OK ||
-      (rc = cuda_err(cudaMalloc(&f->d_split_b, kHalf * sizeof(float2)))) != CORR_OK ||
+      (rc = cuda_err(cudaMalloc(&f->d_split, kHalf * sizeof(float2)))) != CORR_OK ||
       (rc = cuda_err(cudaMalloc(&f->d_eq, eq.size() * sizeof(float)))) != CORR_OK ||
       (rc = cuda_err(cudaMemcpy(f->d_proto, proto.data(), L * sizeof(float),
                                 cudaMemcpyHostToDevice))) != CORR_OK ||
       (rc = cuda_err(cudaMemcpy(f->d_tw_fft, tw_fft.data(), kHalf * sizeof(float2),
                                 cudaMemcpyHostToDevice))) != CORR_OK ||
-      (rc = cuda_err(cudaMemcpy(f->d_split_a, split_a.data(), kHalf * sizeof(float2),
-                                cudaMemcpyHostToDevice))) != CORR_OK ||
-      (rc = cuda_err(cudaMemcpy(f->d_split_b, split_b.data(), kHalf * sizeof(float2),
+      (rc = cuda_err(cudaMemcpy(f->d_split, split.data(), kHalf * sizeof(float2),
                                 cudaMemcpyHostToDevice))) != CORR_OK ||
       (rc = cuda_err(cudaMemcpy(f->d_eq, eq.data(), eq.size() * sizeof(float),
                                 cudaMemcpyHostToDevice))) != CORR_OK) {
@@ -562,7 +577,7 @@ int corr_fengine_run(corr_fengine *f, const int8_t *d_adc, uint8_t *d_out, void 
   const long long work = (long long)f->n_in * ((f->n_spec + kSpecTile - 1) / kSpecTile);
   const int grid = (int)std::min<long long>(work, (long long)f->n_sm * kCtasPerSm * 4);
   fengine_kernel<1><<<grid, kThreads, smem_bytes(), static_cast<cudaStream_t>(stream)>>>(
-      d_adc, f->d_proto, f->d_tw_fft, f->d_split_a, f->d_split_b, f->d_eq, d_out, nullptr, f->n_in, f->n_spec);
+      d_adc, f->d_proto, f->d_tw_fft, f->d_split, f->d_eq, d_out, nullptr, f->n_in, f->n_spec);
   return cuda_err(cudaGetLastError());
 }
 
@@ -572,7 +587,7 @@ int corr_fengine_spectra(corr_fengine *f, const int8_t *d_adc, float *d_spec, vo
   const long long work = (long long)f->n_in * ((f->n_spec + kSpecTile - 1) / kSpecTile);
   const int grid = (int)std::min<long long>(work, (long long)f->n_sm * kCtasPerSm * 4);
   fengine_kernel<0><<<grid, kThreads, smem_bytes(), static_cast<cudaStream_t>(stream)>>>(
-      d_adc, f->d_proto, f->d_tw_fft, f->d_split_a, f->d_split_b, f->d_eq, nullptr,
+      d_adc, f->d_proto, f->d_tw_fft, f->d_split, f->d_eq, nullptr,
       reinterpret_cast<float2 *>(d_spec), f->n_in, f->n_spec);
   return cuda_err(cudaGetLastError());
 }
