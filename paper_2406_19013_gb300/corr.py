@@ -634,8 +634,8 @@ class Server:
 
 class FEngine:
     """The GPU F-engine (corr_fengine_*): int8 ADC streams
-    [n_in][(n_spectra + 3) * 2048] -> packed channel samples
-    uint8[1024][n_in][n_spectra], the X-engine's input order."""
+    [n_in][(n_spectra + 3) * 2048] (starting on a 16-byte boundary) -> packed
+    channel samples uint8[1024][n_in][n_spectra], the X-engine's input order."""
 
     def __init__(self, n_in: int, n_spectra: int, eq=None):
         self._lib = load()

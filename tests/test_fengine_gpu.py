@@ -121,3 +121,22 @@ def test_fengine_paper_size_sampled(corr, synth_mod):
                 seg = x[i:i + 1, k0 * F.P:(k0 + 32 + 3) * F.P]
                 z = F.prequant(seg, eq[i:i + 1].astype(np.float64))
                 _check_codes(codes[:, i:i + 1, k0:k0 + 32].cpu().numpy(), z)
+
+
+def test_fengine_rejects_unaligned_samples(corr):
+    # the samples are copied into shared memory in 16-byte pieces: a stream
+    # that does not start on a 16-byte boundary is refused before any launch
+    import torch
+    n_in, n_spec = 1, 4
+    n = n_in * (n_spec + 3) * F.P
+    base = torch.zeros(n + 16, dtype=torch.int8, device="cuda")
+    with corr.FEngine(n_in, n_spec) as fe:
+        for off in (8, 4, 1):
+            with pytest.raises(corr.CorrError) as ei:
+                fe.run(base[off:off + n])
+            assert ei.value.code == corr.CORR_EINVAL
+            with pytest.raises(corr.CorrError) as ei:
+                fe.spectra(base[off:off + n])
+            assert ei.value.code == corr.CORR_EINVAL
+        fe.run(base[16:16 + n])
+        torch.cuda.synchronize()
