@@ -642,7 +642,7 @@ int corr_plan_cover(int n_in, int cover_kind, uint8_t *cover, int *n_units,
     // a unit of several channels repeats its cover once per channel: count
     // the first channel's segments
     // a pair unit covers its rows once per CTA of the pair, the odd CTA's
-    // pair_rows inputs further on
+    // from row_in1
     for (int rank = 0; rank < (u.pair_rows ? 2 : 1); ++rank)
       for (int sg = 0; sg < u.n_seg; ++sg) {
         const XSeg &s = u.seg[sg];
@@ -652,14 +652,15 @@ int corr_plan_cover(int n_in, int cover_kind, uint8_t *cover, int *n_units,
         const int cpt = s.ch_rows ? xe::kTileInputs / s.ch_rows : 1;
         issued += 64LL * s.n / cpt;  // 128 accumulator rows = 64 inputs x (re, im)
         if (!cover) continue;
-        // the epilogue's mapping: lane rho holds input row_in0 + 8 (rho / 16) + rho % 8,
-        // real part when (rho / 8) is even; column n holds input col_in0 + n
+        // the epilogue's mapping: lane rho holds input row_in0 (row_in1 on the
+        // odd CTA of a pair) + 8 (rho / 16) + rho % 8, real part when (rho / 8)
+        // is even; column n holds input col_blk[n / 64] + n % 64
         for (int rho = 0; rho < 128; ++rho) {
           if ((rho >> 3) & 1) continue;
-          const int i = s.row_in0 + rank * u.pair_rows + 8 * (rho >> 4) + (rho & 7);
+          const int i = (rank ? s.row_in1 : s.row_in0) + 8 * (rho >> 4) + (rho & 7);
           if (i >= n_in || (s.ch_rows && i >= s.ch_rows)) continue;
           for (int n = 0; n < s.n; ++n) {
-            const int j = s.col_in0 + n;
+            const int j = s.col_blk[n >> 6] + (n & 63);
             if (s.ch_rows && j >= s.ch_rows) continue;
             if (j <= i) cover[(size_t)i * n_in + j]++;
           }

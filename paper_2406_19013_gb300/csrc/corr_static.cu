@@ -134,6 +134,7 @@ int plan_single_window(int N, xe::XUnit *units) {
       if (bin_of[t] == b) t_max = std::max(t_max, t);
     xe::XRegion &r = u.reg[0];
     r.in_lo = 0;
+    r.in_lo1 = 0;
     r.n_in = xe::kTileInputs * (t_max + 1);
     r.interleaved = 1;
     r.z_row = 0;
@@ -150,7 +151,8 @@ int plan_single_window(int N, xe::XUnit *units) {
       s.n = std::min(xe::kTileInputs * (t + 1), n16);
       s.tmem_col = u.work;
       s.row_in0 = xe::kTileInputs * t;
-      s.col_in0 = 0;
+      s.row_in1 = s.row_in0;
+      for (int c = 0; c < 4; ++c) s.col_blk[c] = 64 * c;  // columns 0, 1, 2, ...
       u.work += s.n;
       u.n_seg++;
     }

@@ -48,6 +48,7 @@ constexpr int kMaxBlocksPerLaunch = 8;
 // "Q rows"); plain regions store A rows only.
 struct XRegion {
   int in_lo;        // first input
+  int in_lo1;       // first input on the odd CTA of a pair (unused otherwise)
   int n_in;         // inputs staged (multiple of 64; rows past N read as zero)
   // 1: A and Q rows; 2: the interleaved layout with only the A rows written
   // (inputs that are only columns of the unit, next to interleaved rows, so
@@ -66,7 +67,11 @@ struct XSeg {
   int n;         // B rows = output columns (multiple of 16, <= 256)
   int tmem_col;  // first TMEM column of the accumulator
   int row_in0;   // input index of the tile's first row
-  int col_in0;   // input index of the first column
+  int row_in1;   // the same on the odd CTA of a pair (unused otherwise)
+  // input index of the first column of each 64-column block of the
+  // accumulator (column c holds input col_blk[c / 64] + c % 64); one block
+  // per 64 B rows, in the order the B operand takes them
+  int col_blk[4];
   int chan_off;  // channel: the item's first channel + chan_off
   // 0: the tile's rows and columns are inputs of one channel.  Otherwise the
   // 64-row tile holds 64 / ch_rows channels of ch_rows inputs each (row and
@@ -79,10 +84,10 @@ struct XUnit {
   int n_reg, n_seg;
   int n_chan;    // channels one unit covers (its regions and segments name the offsets)
   // 0: one CTA runs the unit.  kPairRows: a CTA pair runs it with M = 256
-  // MMAs; the regions and segments describe the even CTA, and the odd CTA
-  // stages and owns the rows kPairRows inputs further on (its regions'
-  // in_lo and its segments' row_in0 + kPairRows; col_in0 is shared, since
-  // the pair's B operand is the even CTA's B rows followed by the odd one's)
+  // MMAs; both CTAs stage the same layout of regions, the odd CTA from its
+  // regions' in_lo1 and owning its segments' rows from row_in1; a segment's
+  // column blocks are shared, since the pair's B operand is the even CTA's
+  // N / 2 B rows followed by the odd one's
   int pair_rows;
   int z_rows;    // rows staged per chunk (sum over regions)
   int pk_bytes;  // packed bytes per chunk (sum over regions)

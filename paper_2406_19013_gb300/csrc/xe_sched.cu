@@ -24,7 +24,8 @@ void add_seg(XUnit &u, int a_zrow, int b_zrow, int b_sbo, int n, int row_in0, in
   s.n = n;
   s.tmem_col = col;
   s.row_in0 = row_in0;
-  s.col_in0 = col_in0;
+  s.row_in1 = row_in0;
+  for (int b = 0; b < 4; ++b) s.col_blk[b] = col_in0 + 64 * b;
   u.n_seg++;
   u.work += n;
 }
@@ -32,6 +33,7 @@ void add_seg(XUnit &u, int a_zrow, int b_zrow, int b_sbo, int n, int row_in0, in
 void add_reg(XUnit &u, int in_lo, int n_in, int interleaved) {
   XRegion &r = u.reg[u.n_reg];
   r.in_lo = in_lo;
+  r.in_lo1 = in_lo;
   r.n_in = n_in;
   r.interleaved = interleaved;
   r.z_row = u.z_rows;
@@ -129,24 +131,45 @@ std::vector<XUnit> build_schedule(int N, int cover) {
       units.push_back(u);
     }
   } else if (N > 256 && cover == kCoverQuads) {
-    // CTA pairs: rows [R, R + 256) (the even CTA R .. R + 127, the odd one
-    // R + 128 .. R + 255) against columns [P, P + 256), P <= R.  Below the
-    // diagonal the B rows are a plain region (P .. P + 127 on the even CTA,
-    // P + 128 .. on the odd one); on it they are the CTA's own interleaved
-    // A rows.
+    // CTA pairs, blocks of 256 rows [R, R + 256) against 256 columns
+    // [P, P + 256), P <= R, in four row tiles T0..T3 of 64 inputs.
+    //  - Below the diagonal (P < R) the even CTA owns T0 and T1, the odd one
+    //    T2 and T3; their B rows are a plain region, P .. P + 127 on the even
+    //    CTA and P + 128 .. on the odd one.  Two N = 256 MMAs.
+    //  - On the diagonal (P = R) the even CTA owns T0 and T3, the odd one T1
+    //    and T2, and each CTA's own A rows are its B rows: the MMA of T0 and
+    //    T1 (N = 128) takes the first 64 B rows of each CTA, columns T0 T1;
+    //    that of T3 and T2 (N = 256) all of them, columns T0 T3 T1 T2.  That
+    //    issues 3/4 of the work of two N = 256 MMAs over T0 T1 | T2 T3.
     for (int R = 0; R < N; R += 2 * kPairRows) {
       for (int P = 0; P <= R; P += 2 * kPairRows) {
         XUnit u = empty_unit();
         u.pair_rows = kPairRows;
-        add_reg(u, R, kPairRows, 1);
-        int bz = 0, sbo = 2048;
         if (P < R) {
+          add_reg(u, R, kPairRows, 1);
+          u.reg[0].in_lo1 = R + kPairRows;
           add_reg(u, P, kPairRows, 0);
-          bz = u.reg[1].z_row;
-          sbo = 1024;
+          u.reg[1].in_lo1 = P + kPairRows;
+          const int bz = u.reg[1].z_row;
+          for (int t = 0; t < 2; ++t) {
+            add_seg(u, 128 * t, bz, 1024, 2 * kPairRows, R + kTileInputs * t, P);
+            u.seg[t].row_in1 = R + kPairRows + kTileInputs * t;
+          }
+        } else {
+          const int T = kTileInputs;
+          add_reg(u, R, T, 1);  // even: T0, odd: T1
+          u.reg[0].in_lo1 = R + T;
+          add_reg(u, R + 3 * T, T, 1);  // even: T3, odd: T2
+          u.reg[1].in_lo1 = R + 2 * T;
+          add_seg(u, 0, 0, 2048, 2 * T, R, R);
+          u.seg[0].row_in1 = R + T;
+          u.seg[0].col_blk[1] = R + T;
+          add_seg(u, 128, 0, 2048, 4 * T, R + 3 * T, R);
+          u.seg[1].row_in1 = R + 2 * T;
+          u.seg[1].col_blk[1] = R + 3 * T;
+          u.seg[1].col_blk[2] = R + T;
+          u.seg[1].col_blk[3] = R + 2 * T;
         }
-        for (int t = 0; t < 2; ++t)
-          add_seg(u, 128 * t, bz, sbo, 2 * kPairRows, R + kTileInputs * t, P);
         units.push_back(u);
       }
     }

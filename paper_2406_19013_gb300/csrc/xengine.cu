@@ -37,11 +37,11 @@
 // bounded by a timeout; on expiry the kernel drains its own copies and MMAs,
 // frees TMEM and reports through *status.
 // The CTA-pair instance (PAIR) runs clusters of two CTAs on two SMs: each
-// stages and unpacks 128 rows and half of a 256-column B operand, the even
-// CTA's two issuers run M = 256 MMAs (cta_group::2) over both halves and
-// commit to both CTAs' barriers, one thread of the odd CTA forwards its
-// unpack warps' stage arrivals to the even CTA, and each CTA folds its own
-// 128 TMEM lanes.
+// stages and unpacks two row tiles and half of a B operand of up to 256
+// columns, the even CTA's two issuers run M = 256 MMAs (cta_group::2) over
+// both halves and commit to both CTAs' barriers, one thread of the odd CTA
+// forwards its unpack warps' stage arrivals to the even CTA, and each CTA
+// folds its own 128 TMEM lanes.
 #include <cuda.h>
 
 #include <cstring>
@@ -145,9 +145,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (PAIR) cluster_sync();
   tc_fence_after();
   const uint32_t tmem = misc[0];
-  // rank in the pair, and the rows of the odd CTA's share of a pair unit
+  // rank in the pair (the odd CTA stages its regions from in_lo1 and owns
+  // its segments' rows from row_in1)
   const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
-  const int rank_rows = PAIR ? kPairRows * (int)rank : 0;
 
   int it0, it1, it_step;
   if (p.items) {
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           armed_ph[s] = ph;
           const uint32_t dst0 = smem_u32(pk_buf + (size_t)s * p.pk_stage_bytes);
           for (int r = 0; r < n_reg; ++r) {
-            const int in_lo = u->reg[r].in_lo + rank_rows, n_in = u->reg[r].n_in;
+            const int in_lo = rank ? u->reg[r].in_lo1 : u->reg[r].in_lo, n_in = u->reg[r].n_in;
             const int off = u->reg[r].pk_off;
             const int ch = item.chan + u->reg[r].chan_off;  // past the last: zero fill
             for (int bx = 0; bx < n_in; bx += kTileInputs) {
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // block ci (the same for every lane of the warp, whose 16 rows lie in
         // one block of at least 16)
         const int rpc = sgm.ch_rows;
-        const int il = sgm.row_in0 + rank_rows + 8 * g + l_in;
+        const int il = (rank ? sgm.row_in1 : sgm.row_in0) + 8 * g + l_in;
         const int ci = rpc ? il / rpc : 0;
         const int c = item.chan + sgm.chan_off + ci;
         if (c >= pb.n_chan) continue;  // a multi-channel unit's missing last channels
@@ -520,7 +520,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             re[e] = is_im ? other : mine;
             im[e] = is_im ? mine : other;
           }
-          int j0 = sgm.col_in0 + cb + (is_im ? 8 : 0);
+          const int cc = cb + (is_im ? 8 : 0);  // the 8 columns of this lane
+          int j0 = sgm.col_blk[cc >> 6] + (cc & 63);
           bool blk_ok = true;  // the 8 columns lie in this row's channel block
           if (rpc) {
             blk_ok = j0 / rpc == ci;

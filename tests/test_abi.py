@@ -185,13 +185,26 @@ def test_item_split_quad_cover(corr, args):
 
 
 def test_quad_cover_units_are_pair_units(corr):
-    """Each quad unit's 256 rows are covered by its two CTAs: the cover view
-    counts the odd CTA's rows 128 inputs further on, and 2048 inputs need 36
-    units (8 row blocks x up to 8 column pieces), 8 of them on the diagonal."""
+    """Each quad unit's 256 rows are covered by its two CTAs (the cover view
+    reads the odd CTA's rows and the column blocks the way the epilogue
+    does), and 2048 inputs need 36 units (8 row blocks x up to 8 column
+    pieces).  The 28 below the diagonal issue two N = 256 MMAs per CTA; the 8
+    on it pair row tiles T0 and T1 against 128 columns and T3 and T2 against
+    256, three quarters of that work."""
     n_units, issued, got = corr.plan_cover(2048, 3, with_cover=True)
     assert n_units == 36
-    assert issued == 36 * 2 * 2 * 64 * 256  # units x CTAs x row tiles x 64 inputs x 256 columns
+    # units x CTAs x (row tiles x 64 inputs x columns)
+    assert issued == 28 * 2 * (2 * 64 * 256) + 8 * 2 * (64 * 128 + 64 * 256)
     assert np.array_equal(got, np.tril(np.ones((2048, 2048), dtype=np.uint8)))
+
+
+@pytest.mark.parametrize("n", [257, 300, 384, 512, 600, 1000])
+def test_quad_cover_is_the_triangle_once(corr, n):
+    # ragged sizes too: rows and columns past N are staged as zeros and never folded
+    _, issued, got = corr.plan_cover(n, 3, with_cover=True)
+    assert np.array_equal(got, np.tril(np.ones((n, n), dtype=np.uint8)))
+    blocks = (n + 255) // 256
+    assert issued == (blocks * (blocks - 1) // 2) * 2 * (2 * 64 * 256) + blocks * 2 * (64 * 128 + 64 * 256)
 
 
 def test_plan_items_rejects(corr):
