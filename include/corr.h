@@ -173,7 +173,9 @@ int corr_plan(int n_in, uint8_t *cover, int *n_units, long long *issued_cmacs);
  *   QUADS:  N > 256.  Blocks of 256 rows against 256-column pieces of their
  *           strip, each run by a pair of CTAs on two SMs (a 2-CTA cluster):
  *           each CTA stages 128 of the rows and half of the piece's columns,
- *           and the pair's M = 256 tensor-core MMAs share the columns.
+ *           and the pair's M = 256 tensor-core MMAs share the columns.  On
+ *           the diagonal the CTAs take row tiles 0 and 3, and 1 and 2, so
+ *           that tiles 0 and 1 run against 128 columns only.
  *           Contexts use it only when CORR_CMAC_KERNEL=pair is set.
  * WINDOW and STRIPS fall back to PAIRS above 256 inputs, QUADS to PAIRS at
  * 256 and below.  CORR_CMAC_KERNEL=pair in the environment makes contexts of
